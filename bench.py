@@ -1,0 +1,403 @@
+"""Benchmark of the GOVM shortest-path solver on one GB300 (or N replicas).
+
+Default workload (one "step"): the 64 sources of the R-MAT scale-22 graph
+(a,b,c,d = .57,.19,.19,.05, edge factor 16, duplicates removed, uint32
+weights U[1,255]), each solved as its own SSSP through the C ABI
+(dawn_sssp: init, every GOVM step and the dist/parent output in one
+persistent launch).  GTEPS = edges of the largest WCC / solve time.
+
+Printed (rank 0, one JSON line): device-timed GTEPS over K steps, the
+roofline of the persistent kernel (algorithmic bytes from the solver's own
+counters / CUDA-event launch time, against the measured HBM copy bandwidth),
+the end-to-end GTEPS through the C ABI from pinned host buffers (graph copy
+in, solves, dist + parent copied out), the CPU oracle on a bounded sample, and
+the SM clocks sampled during the timed region.
+
+Other workloads (--workload): grid (2048^2 fp32 grid with shortcuts, 16
+sources), batched (R-MAT s18 with 1024 sources in msssp launches vs a loop
+of single solves; 64 uneven ER graphs in one multi-root launch vs a loop),
+diff (R-MAT s16 fp32: forward, forward+backward, plain solve), tiny
+(ER n=1024).
+
+--impl reference times the CPU oracle (the literal GOVM iteration) on the
+host cores instead; under torchrun only rank 0 runs it.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+HBM_FALLBACK_GBS = 6800.0
+METRIC = "GTEPS and % HBM roofline for SSSP on 1 GB300; batched/backward vs plain solver"
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def measured_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons (200 ms)."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200", "-i", str(self.index)], stdout=subprocess.PIPE,
+                                      stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.p is not None:
+            time.sleep(0.25)
+            self.p.terminate()
+            out, _ = self.p.communicate(timeout=10)
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ workloads
+
+def make_workload(name: str, rank: int = 0, world: int = 1):
+    import graphgen as gg
+    if name == "rmat22":
+        wl = gg.rmat_u32(22, 16, nsrc=64 * world, seed=0)
+        wl.sources = wl.sources[rank * 64:(rank + 1) * 64]
+        return wl
+    if name == "grid":
+        wl = gg.grid_f32(2048, 0.01, nsrc=16 * world, seed=0)
+        wl.sources = wl.sources[rank * 16:(rank + 1) * 16]
+        return wl
+    if name == "tiny":
+        return gg.tiny_er()
+    raise ValueError(name)
+
+
+def bytes_alg(st):
+    """Algorithmic bytes of one solve from its counters: 16 B per frontier
+    vertex (id, row_ptr pair, own distance), 12 B per scanned edge (col,
+    weight, target state filter read), 12 B per strict update (8 B atomic,
+    4 B queue append)."""
+    return 16 * st["frontier_sum"] + 12 * st["edges_scanned"] + 12 * st["updates"]
+
+
+# --------------------------------------------------------------- our solver
+
+def run_sssp_bench(args, wl, device, world, rank):
+    import torch
+    import paper_2306_07872_gb300 as dawn
+
+    torch.cuda.set_device(device)
+    stream = torch.cuda.current_stream()
+    g = dawn.Graph(wl.row_ptr, wl.col, wl.weights, device=device)
+    S = len(wl.sources)
+    dist = torch.empty((S, wl.n), dtype=g.dist_dtype, device=device)
+    par = torch.empty((S, wl.n), dtype=torch.int32, device=device)
+    srcs = [int(s) for s in wl.sources]
+
+    def step(evs=None):
+        for i, s in enumerate(srcs):
+            if evs is not None:
+                evs[i][0].record(stream)
+            dawn.dawn_sssp(g.handle, s, dist[i], par[i], None)
+            if evs is not None:
+                evs[i][1].record(stream)
+
+    # warm-up (untimed)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    g.check()
+    # counters of one pass (untimed): algorithmic bytes, mu, steps
+    stats = []
+    for s in srcs:
+        dawn.dawn_sssp(g.handle, s, dist[0], par[0], None)
+        stats.append(dawn.dawn_get_stats(g.handle))
+    # timed region
+    evs = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in srcs]
+           for _ in range(args.steps)]
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    barrier(world)
+    torch.cuda.synchronize()
+    with Clocks(device) as clk:
+        t0.record(stream)
+        for k in range(args.steps):
+            step(evs[k])
+        t1.record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    g.check()
+    elapsed = t0.elapsed_time(t1) / 1e3
+    elapsed = max_over_ranks(elapsed, world)
+    launch_ms = np.array([[a.elapsed_time(b) for a, b in row] for row in evs])  # [K, S]
+    per_src_ms = launch_ms.mean(axis=0)
+    b_alg = np.array([bytes_alg(st) for st in stats], dtype=np.float64)
+    achieved_gbs = float((b_alg / (per_src_ms / 1e3)).mean() / 1e9)
+    achieved_gbs_total = float(b_alg.sum() / (per_src_ms.sum() / 1e3) / 1e9)
+    mu = float(np.mean([st["updates"] for st in stats]))
+    res = {
+        "elapsed": elapsed,
+        "gteps": S * world * wl.e_wcc / elapsed / 1e9,
+        "launch_ms_mean": float(launch_ms.mean()),
+        "launch_ms_median": float(np.median(launch_ms)),
+        "gteps_median": float(np.median(wl.e_wcc / (per_src_ms / 1e3) / 1e9)),
+        "gteps_hmean": float(S / np.sum(1.0 / (wl.e_wcc / (per_src_ms / 1e3) / 1e9))),
+        "achieved_gbs": achieved_gbs_total,
+        "achieved_gbs_mean_of_launches": achieved_gbs,
+        "b_alg_mean": float(b_alg.mean()),
+        "updates_mean": mu,
+        "edges_scanned_mean": float(np.mean([st["edges_scanned"] for st in stats])),
+        "steps_mean": float(np.mean([st["steps"] for st in stats])),
+        "clocks": clk.summary(),
+        "launches": S * args.steps,
+        "stats0": stats[0],
+    }
+    g.close()
+    del dist, par
+    torch.cuda.empty_cache()
+    return res
+
+
+def run_e2e(args, wl, device, world):
+    """Same metric through the C ABI from pinned host buffers: per step the
+    graph is copied in and validated (dawn_create_graph with host inputs),
+    every source is solved, and dist + parent are copied back to pinned
+    host memory."""
+    import torch
+    import paper_2306_07872_gb300 as dawn
+
+    torch.cuda.set_device(device)
+    rp = torch.from_numpy(wl.row_ptr).pin_memory()
+    cl = torch.from_numpy(wl.col).pin_memory()
+    w = torch.from_numpy(wl.weights).pin_memory()
+    S = len(wl.sources)
+    dist_dtype = torch.uint32 if wl.weights.dtype == np.uint32 else torch.float32
+    h_dist = torch.empty((S, wl.n), dtype=dist_dtype).pin_memory()
+    h_par = torch.empty((S, wl.n), dtype=torch.int32).pin_memory()
+    dist = torch.empty((S, wl.n), dtype=dist_dtype, device=device)
+    par = torch.empty((S, wl.n), dtype=torch.int32, device=device)
+    stream = torch.cuda.current_stream()
+    srcs = [int(s) for s in wl.sources]
+
+    def step():
+        h = dawn.dawn_create_graph(rp, cl, w, stream)
+        for i, s in enumerate(srcs):
+            dawn.dawn_sssp(h, s, dist[i], par[i], None, stream)
+        h_dist.copy_(dist, non_blocking=True)
+        h_par.copy_(par, non_blocking=True)
+        code = dawn.dawn_status(h, True)
+        dawn.dawn_destroy(h)
+        if code:
+            raise dawn.DawnError(code, "e2e solve")
+
+    step()
+    torch.cuda.synchronize()
+    steps = max(1, min(args.steps, 3))
+    barrier(world)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for _ in range(steps):
+        step()
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t
+    barrier(world)
+    el = max_over_ranks(el, world)
+    h2d = wl.row_ptr.nbytes + wl.col.nbytes + wl.weights.nbytes
+    d2h = h_dist.numel() * 4 + h_par.numel() * 4
+    return {"value": S * world * wl.e_wcc / (el / steps) / 1e9, "unit": "GTEPS", "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "steps": steps, "ms_per_step": el / steps * 1e3}
+
+
+def cpu_baseline(wl, budget_s: float = 20.0):
+    """The oracle's literal GOVM iteration (Algorithm 2) on the host cores,
+    one source per thread, on a bounded sample of the sources."""
+    import oracle
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    threads = max(1, min(cores, 16, len(wl.sources)))
+    # one probe solve sizes the sample to the time budget
+    t, _ = oracle.timed_govm(wl.row_ptr, wl.col, wl.weights, [int(wl.sources[0])], threads=1)
+    rounds = max(1, int(budget_s / max(t, 1e-3) / 2))
+    nsrc = min(len(wl.sources), threads * rounds)
+    sample = [int(s) for s in wl.sources[:nsrc]]
+    el, res = oracle.timed_govm(wl.row_ptr, wl.col, wl.weights, sample, threads=threads)
+    return {"value": len(sample) * wl.e_wcc / el / 1e9, "unit": "GTEPS", "cores": threads, "kind": "oracle",
+            "sample": f"{len(sample)} of the {len(wl.sources)} sources, literal GOVM (Algorithm 2), "
+                      f"one source per thread, {threads} threads, {el:.1f} s",
+            "mu_oracle": float(np.mean([r[1]["mu"] for r in res]))}
+
+
+# ----------------------------------------------------------------- plumbing
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as tdist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if tdist.get_backend() == "nccl" else "cpu")
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def init_dist(world, local):
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        tdist.init_process_group(backend)
+
+
+def main_reference(args):
+    world, rank, local = dist_env()
+    if rank != 0:
+        return
+    wl = make_workload(args.workload if args.workload in ("rmat22", "grid", "tiny") else "rmat22")
+    import oracle
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    threads = max(1, min(cores, 16))
+    t, _ = oracle.timed_govm(wl.row_ptr, wl.col, wl.weights, [int(wl.sources[0])], threads=1)
+    per_step = max(1, min(len(wl.sources), threads * max(1, int(8.0 / max(t, 1e-3)))))
+    step_sources = [int(s) for s in wl.sources[:per_step]]
+    for _ in range(args.warmup):
+        oracle.timed_govm(wl.row_ptr, wl.col, wl.weights, step_sources[:threads], threads=threads)
+    total = 0.0
+    for _ in range(args.steps):
+        el, _ = oracle.timed_govm(wl.row_ptr, wl.col, wl.weights, step_sources, threads=threads)
+        total += el
+    value = args.steps * len(step_sources) * wl.e_wcc / total / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": wl.wtype, "data": "synthetic",
+            "config": {"workload": wl.name, "n": wl.n, "m": wl.m, "e_wcc": wl.e_wcc,
+                       "sources_per_step": len(step_sources)},
+            "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": threads, "kind": "oracle",
+                             "sample": f"{len(step_sources)} sources per step, literal GOVM (Algorithm 2), "
+                                       f"one source per thread"},
+            "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main_ours(args):
+    world, rank, local = dist_env()
+    init_dist(world, local)
+    device = local
+    import torch
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (the solver has no CPU path)")
+    if args.workload in ("rmat22", "grid", "tiny"):
+        t = time.time()
+        wl = make_workload(args.workload, rank, world)
+        log(f"[bench] {wl.name}: n={wl.n} m={wl.m} e_wcc={wl.e_wcc} sources={len(wl.sources)} "
+            f"(generated in {time.time() - t:.1f} s)")
+        res = run_sssp_bench(args, wl, device, world, rank)
+        log(f"[bench] device: {res['gteps']:.2f} GTEPS, {res['launch_ms_mean']:.3f} ms/launch, "
+            f"B_alg {res['b_alg_mean'] / 1e9:.3f} GB, {res['achieved_gbs']:.0f} GB/s, steps {res['steps_mean']:.1f}")
+        e2e = run_e2e(args, wl, device, world) if not args.no_e2e else None
+        cpu = cpu_baseline(wl, args.cpu_budget) if (rank == 0 and not args.no_cpu) else None
+        if rank != 0:
+            return
+        peak, peak_kind = measured_peak()
+        line = {
+            "metric": METRIC, "value": res["gteps"], "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": res["elapsed"] / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": wl.wtype, "data": "synthetic",
+            "config": {"workload": wl.name, "n": wl.n, "m": wl.m, "e_wcc": wl.e_wcc, "s_wcc": wl.s_wcc,
+                       "sources_per_step": len(wl.sources) * world, "parallelism": f"replicas{world}",
+                       "l2": "inputs larger than L2 (CSR col+w %.0f MB > 129 MB); no flush" %
+                             ((wl.col.nbytes + wl.weights.nbytes) / 1e6)},
+            "roofline": {"bound": "hbm", "achieved": res["achieved_gbs"], "peak": peak, "unit": "GB/s",
+                         "frac": res["achieved_gbs"] / peak, "traffic": None,
+                         "peak_kind": f"{peak_kind} copy bandwidth", "kernel": "govm_kernel",
+                         "b_alg_per_launch": res["b_alg_mean"], "launch_ms": res["launch_ms_mean"],
+                         "frac_of_8000": res["achieved_gbs"] / 8000.0},
+            "gteps_median": res["gteps_median"], "gteps_hmean_per_launch": res["gteps_hmean"],
+            "solver": {"steps_mean": res["steps_mean"], "updates_mean": res["updates_mean"],
+                       "edges_scanned_mean": res["edges_scanned_mean"],
+                       "edges_scanned_over_e_wcc": res["edges_scanned_mean"] / wl.e_wcc},
+            "e2e": e2e, "gpu_launches": res["launches"], "clocks": res["clocks"], "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    else:
+        raise SystemExit(f"unknown workload {args.workload}")
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="rmat22")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        log("[bench] warm-up raised to 3 steps")
+        args.warmup = 3
+    if args.impl == "reference":
+        main_reference(args)
+    else:
+        main_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,197 @@
+/*
+ * dawn.h -- C ABI of the GB300 (sm_103a) weighted-DAWN shortest-path library.
+ *
+ * The library implements the GOVM iteration of weighted DAWN (arxiv
+ * 2306.07872, Section 3.4, Algorithm 2): the distance vector alpha is
+ * multiplied by the CSR adjacency matrix in the (min, +) semiring, but only
+ * the rows of vertices whose distance changed in the previous step (the
+ * frontier delta) are expanded; vertices whose distance changes in this step
+ * form the next frontier (beta); the iteration stops when a step changes
+ * nothing.  This yields single-source shortest paths (SSSP), and multi-source
+ * / all-pairs shortest paths as repeated SSSP (Section 3.4, "time complexity
+ * of DAWN for APSP tasks"; Section 1, contribution 5 on MSSP).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Every function returns a dawn_status_code value; nothing throws across the ABI.
+ *  - Arguments checked on the host (sizes, pointers, scalar ids) fail
+ *    synchronously.  Arguments that live in device memory (source / root
+ *    arrays) are checked by the kernel, which then skips the solve and leaves
+ *    the error in the graph's status word: read it with dawn_status().
+ *  - Solves are stream ordered: they enqueue work on `stream` (a cudaStream_t,
+ *    NULL for the legacy default stream) and return without synchronising.
+ *    Device-side failures (step cap, barrier timeout, invalid device input)
+ *    are reported through dawn_status().
+ *  - Output arrays are caller-allocated DEVICE buffers on the graph's device.
+ *  - Distances: uint32 graphs report uint32 distances with 0xFFFFFFFF for
+ *    unreachable vertices; float32 graphs report float32 distances, each the
+ *    round-to-nearest left fold fl(...fl(0 + w1) + ... + wk) along a shortest
+ *    path, with +inf for unreachable vertices.
+ *  - Parents: parent[v] is the tail u of the lowest-index CSR edge e = (u->v)
+ *    with fl(dist[u] + w[e]) == dist[v]; parent[source] = source;
+ *    parent[unreachable] = -1.  parent_edge[v] is that edge index e, or -1
+ *    for sources and unreachable vertices.  (The paper returns distances only;
+ *    the parent rule is this library's definition.)
+ *  - A graph handle must not be used by two solves that overlap on the GPU
+ *    (one stream at a time per handle); solves on different handles may run
+ *    concurrently.
+ */
+#ifndef DAWN_H
+#define DAWN_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dawn_graph_s *dawn_graph; /* opaque, owned by the library */
+
+typedef enum { DAWN_W_U32 = 0, DAWN_W_F32 = 1 } dawn_wtype;
+
+typedef enum {
+  DAWN_OK = 0,
+  DAWN_ERR_INVALID = 1,       /* bad argument, malformed CSR, bad weight, source out of range */
+  DAWN_ERR_OOM = 2,           /* device allocation failed */
+  DAWN_ERR_CUDA = 3,          /* a CUDA runtime call failed (launch, copy, ...) */
+  DAWN_ERR_NOT_CONVERGED = 4, /* the step cap (n steps, as in Algorithm 2) was reached */
+  DAWN_ERR_TIMEOUT = 5,       /* a bounded wait inside the solver ran out; the kernel returned */
+  DAWN_ERR_BOUNDS = 6         /* an internal capacity check failed; the kernel returned */
+} dawn_status_code;
+
+/* Per-solve counters summed over all instances of the last solve. */
+typedef struct {
+  int64_t steps;         /* GOVM steps executed (frontier non-empty) */
+  int64_t frontier_sum;  /* sum over steps of |delta| (frontier vertices, out-degree >= 1) */
+  int64_t edges_scanned; /* sum over steps of the frontier's out-edges (edges relaxed) */
+  int64_t updates;       /* strict distance decreases (path updates, the paper's mu numerator) */
+  int64_t instances;     /* instances solved by the last call */
+} dawn_stats;
+
+/*
+ * Create a graph from a CSR adjacency matrix (Section 3.2: A_CSR.row_ptr,
+ * A_CSR.col, A_CSR.value).
+ *   n            number of vertices, 1 <= n < 2^31
+ *   m            number of edges, 0 <= m < 2^31
+ *   row_ptr      int32[n+1], row_ptr[0] = 0, non-decreasing, row_ptr[n] = m
+ *   col_idx      int32[m], every entry in [0, n); parallel edges and
+ *                self-loops are allowed
+ *   weights      uint32[m] (wtype DAWN_W_U32) or float32[m] (DAWN_W_F32);
+ *                float weights must be finite and >= 0; uint32 weights must
+ *                satisfy n * max(w) < 0xFFFFFFFF so that no path sum can
+ *                reach the unreachable sentinel
+ *   inputs_on_device  0: the three arrays are host memory; 1: device memory
+ *   stream       stream for the copies and the validation kernel
+ *   out          receives the handle
+ * The library copies the arrays; the caller keeps ownership of its inputs.
+ * Validation runs on the device and is synchronous (the call waits for it).
+ * Errors: DAWN_ERR_INVALID (malformed input), DAWN_ERR_OOM, DAWN_ERR_CUDA.
+ */
+int dawn_create_graph(int32_t n, int64_t m, const int32_t *row_ptr, const int32_t *col_idx,
+                      const void *weights, int wtype, int inputs_on_device, void *stream,
+                      dawn_graph *out);
+
+/*
+ * Replace the edge weights (same type and count as at creation), e.g. after
+ * a gradient step.  Same validation and ownership rules as creation.
+ */
+int dawn_set_weights(dawn_graph g, const void *weights, int inputs_on_device, void *stream);
+
+/*
+ * Pre-size the solver workspace for batches of up to k instances (optional;
+ * solves grow it on demand).  Call before capturing solves into a CUDA
+ * graph, since growing the workspace allocates device memory.
+ */
+int dawn_reserve(dawn_graph g, int32_t k);
+
+/*
+ * Single-source shortest paths by the GOVM iteration (Algorithm 2).
+ *   source       vertex id in [0, n) (checked synchronously)
+ *   dist         device uint32[n] or float32[n] (per the graph's weight type)
+ *   parent       device int32[n] or NULL
+ *   parent_edge  device int32[n] or NULL
+ * One persistent kernel performs initialisation, every GOVM step (with a
+ * device-wide barrier and no host round trip per step) and the output.
+ */
+int dawn_sssp(dawn_graph g, int32_t source, void *dist, int32_t *parent, int32_t *parent_edge,
+              void *stream);
+
+/*
+ * Multi-source shortest paths: k independent SSSP instances, one per source,
+ * relaxed together with per-instance frontiers (Section 1, contribution 5;
+ * the paper's "each thread accesses paths from different starting points",
+ * Section 3.5).  APSP is the case sources = 0..n-1.
+ *   sources      device int32[k]; an entry outside [0, n) makes the solve
+ *                fail with DAWN_ERR_INVALID in dawn_status()
+ *   k            number of instances, k >= 1
+ *   dist         device [k][n] (row i holds the distances from sources[i])
+ *   parent       device int32[k][n] or NULL
+ * Large k is processed in chunks of instances, each chunk one persistent
+ * launch.
+ */
+int dawn_msssp(dawn_graph g, const int32_t *sources, int32_t k, void *dist, int32_t *parent,
+               void *stream);
+
+/*
+ * One shortest-path forest grown from several roots at distance 0 (all roots
+ * are "sources" for the index != source guard of Algorithm 2).  On a graph
+ * that is the disjoint union of many graphs with one root each, this solves
+ * every graph in one launch.
+ *   roots        device int32[k] (duplicates allowed), k >= 1
+ *   dist, parent, parent_edge  as for dawn_sssp (parent[root] = root)
+ */
+int dawn_sssp_roots(dawn_graph g, const int32_t *roots, int32_t k, void *dist, int32_t *parent,
+                    int32_t *parent_edge, void *stream);
+
+/*
+ * Backward pass of dist with respect to the edge weights (float32 graphs).
+ * dist[v] is the sum of the weights along v's tree path, so for a loss L,
+ * dL/dw[e] = sum of dL/ddist[t] over the subtree below tree edge e, and 0 for
+ * edges off the tree.  The parent tree from the forward solve is the only
+ * saved state.
+ *   parent_edge  device int32[n] from dawn_sssp / dawn_sssp_roots
+ *   grad_dist    device float32[n] (dL/ddist; entries of unreachable
+ *                vertices are ignored)
+ *   grad_w       device float32[m], overwritten
+ * A parent_edge array that contains a cycle makes the call fail with
+ * DAWN_ERR_INVALID in dawn_status().
+ */
+int dawn_sssp_backward(dawn_graph g, const int32_t *parent_edge, const float *grad_dist, float *grad_w,
+                       void *stream);
+
+/*
+ * Device-side status of the last solve on this handle (DAWN_OK or an error
+ * code).  With sync != 0 the call first waits for the last stream used by the
+ * handle; with sync == 0 it reads the status without waiting (it may be
+ * stale).
+ */
+int dawn_status(dawn_graph g, int sync);
+
+/* Counters of the last solve (waits for it). */
+int dawn_get_stats(dawn_graph g, dawn_stats *out);
+
+/*
+ * Tuning and test options.
+ *   DAWN_OPT_MAX_STEPS     step cap (default n, as in "while step < n")
+ *   DAWN_OPT_WAIT_LIMIT_NS bound on every in-kernel wait (default 4e9 ns)
+ *   DAWN_OPT_GRID_BLOCKS   persistent grid size (0 = all co-resident blocks)
+ *   DAWN_OPT_TEST_STALL    1: block 0 waits on a flag nothing sets, so the
+ *                          bounded waits run out (tests DAWN_ERR_TIMEOUT)
+ */
+enum { DAWN_OPT_MAX_STEPS = 1, DAWN_OPT_WAIT_LIMIT_NS = 2, DAWN_OPT_GRID_BLOCKS = 3, DAWN_OPT_TEST_STALL = 4 };
+int dawn_set_option(dawn_graph g, int option, int64_t value);
+
+/* Basic graph facts: n, m and the weight type. */
+int dawn_graph_info(dawn_graph g, int32_t *n, int64_t *m, int *wtype);
+
+/* Human-readable name of a status code (static string). */
+const char *dawn_status_string(int code);
+
+/* Free the graph and its device memory.  NULL is allowed. */
+void dawn_destroy(dawn_graph g);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DAWN_H */

@@ -1,0 +1,468 @@
+// C ABI of libdawn (declared in include/dawn.h): graph ingest and
+// validation, solver workspace, launches of the persistent GOVM kernel, the
+// backward pass, status and counters.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+#include <new>
+
+#include "dawn_common.cuh"
+
+using dawn::DeviceCtl;
+using dawn::GovmParams;
+
+struct dawn_graph_s {
+  int32_t n = 0;
+  int64_t m = 0;
+  int wtype = 0;
+  int device = 0;
+  int sms = 0;
+  int32_t *row_ptr = nullptr;
+  int32_t *col = nullptr;
+  uint32_t *w = nullptr;
+  int32_t *src = nullptr;
+  // solver workspace for up to ws_k instances
+  int32_t ws_k = 0;
+  unsigned long long *state = nullptr;
+  uint32_t *bm0 = nullptr, *bm1 = nullptr;
+  int2 *q0 = nullptr, *q1 = nullptr;
+  int32_t *t0 = nullptr, *t1 = nullptr;
+  unsigned long long *tails = nullptr;
+  int64_t words = 0, tiles_cap = 0;
+  DeviceCtl *ctl = nullptr;
+  unsigned *vflags = nullptr;  // validation flags [0] and max weight [1]
+  // options
+  int64_t max_steps = 0;
+  unsigned long long wait_limit_ns = 4000000000ull;
+  int grid_blocks = 0;
+  int test_stall = 0;
+  int last_k = 0;
+  cudaStream_t last_stream = nullptr;
+};
+
+namespace {
+
+enum : unsigned { kBadRowPtr = 1u, kBadCol = 2u, kBadWeight = 4u };
+
+__global__ void validate_kernel(const int32_t *row_ptr, const int32_t *col, const uint32_t *w, int32_t n, int64_t m,
+                                int is_f32, unsigned *flags) {
+  const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long gsize = (long long)gridDim.x * blockDim.x;
+  unsigned bad = 0, wmax = 0;
+  for (long long v = gtid; v <= n; v += gsize) {
+    const int32_t r = row_ptr[v];
+    if (v == 0 && r != 0) bad |= kBadRowPtr;
+    if (v == n && (int64_t)r != m) bad |= kBadRowPtr;
+    if (v < n && row_ptr[v + 1] < r) bad |= kBadRowPtr;
+  }
+  for (long long e = gtid; e < m; e += gsize) {
+    const int32_t c = col[e];
+    if (c < 0 || c >= n) bad |= kBadCol;
+    const uint32_t x = w[e];
+    if (is_f32) {
+      const float f = __uint_as_float(x);
+      if (!(f >= 0.0f) || isinf(f)) bad |= kBadWeight;  // NaN fails f >= 0
+    } else {
+      wmax = max(wmax, x);
+    }
+  }
+  for (int d = 16; d > 0; d >>= 1) {
+    bad |= __shfl_xor_sync(0xFFFFFFFFu, bad, d);
+    wmax = max(wmax, __shfl_xor_sync(0xFFFFFFFFu, wmax, d));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (bad) atomicOr(flags, bad);
+    if (wmax) atomicMax(flags + 1, wmax);
+  }
+}
+
+// src[e] = tail of edge e (one warp per row).
+__global__ void edge_tail_kernel(const int32_t *row_ptr, int32_t n, int32_t *src) {
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  for (long long u = warp; u < n; u += nwarps) {
+    const int32_t b = row_ptr[u], e = row_ptr[u + 1];
+    for (int32_t i = b + lane; i < e; i += 32) src[i] = (int32_t)u;
+  }
+}
+
+__global__ void zero_f32_kernel(float *p, int64_t count) {
+  const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long gsize = (long long)gridDim.x * blockDim.x;
+  for (long long i = gtid; i < count; i += gsize) p[i] = 0.0f;
+}
+
+// Backward of dist w.r.t. the weights along the parent tree: every vertex v
+// with a non-zero dL/ddist[v] adds it to each tree edge on its path to the
+// root, so grad_w[e] ends up as the sum of dL/ddist over the subtree below e.
+// A walk longer than n edges means the parent array has a cycle.
+__global__ void backward_walk_kernel(const int32_t *parent_edge, const float *grad_dist, const int32_t *src,
+                                     float *grad_w, int32_t n, int64_t m, DeviceCtl *ctl) {
+  const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long gsize = (long long)gridDim.x * blockDim.x;
+  for (long long v = gtid; v < n; v += gsize) {
+    const float g = grad_dist[v];
+    int32_t e = parent_edge[v];
+    if (g == 0.0f || e < 0) continue;
+    int32_t hops = 0;
+    while (e >= 0) {
+      if ((int64_t)e >= m) {
+        atomicCAS(&ctl->status, 0, (int)DAWN_ERR_INVALID);
+        break;
+      }
+      atomicAdd(grad_w + e, g);
+      const int32_t u = src[e];
+      e = parent_edge[u];
+      if (++hops > n) {
+        atomicCAS(&ctl->status, 0, (int)DAWN_ERR_INVALID);
+        break;
+      }
+    }
+  }
+}
+
+int cuda_fail(cudaError_t e) {
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return DAWN_ERR_OOM;
+  }
+  return DAWN_ERR_CUDA;
+}
+
+template <typename T>
+int dalloc(T **p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return cuda_fail(e);
+  }
+  return DAWN_OK;
+}
+
+void free_workspace(dawn_graph g) {
+  cudaFree(g->state);
+  cudaFree(g->bm0);
+  cudaFree(g->bm1);
+  cudaFree(g->q0);
+  cudaFree(g->q1);
+  cudaFree(g->t0);
+  cudaFree(g->t1);
+  cudaFree(g->tails);
+  g->state = nullptr;
+  g->bm0 = g->bm1 = nullptr;
+  g->q0 = g->q1 = nullptr;
+  g->t0 = g->t1 = nullptr;
+  g->tails = nullptr;
+  g->ws_k = 0;
+}
+
+// Largest number of instances one launch may hold: the per-block instance
+// prefix, the int32 tile numbering and a device-memory budget.
+int32_t max_chunk(dawn_graph g) {
+  const int64_t tiles_cap = g->m / dawn::kTile + 2;
+  int64_t by_tiles = (int64_t)0x7FFFFFFF / tiles_cap;
+  const int64_t per_inst = (int64_t)g->n * (8 + 16) + 2 * 4 * ((g->n + 31) / 32) + 2 * 4 * tiles_cap + 24;
+  size_t free_b = 0, total_b = 0;
+  int64_t budget = (int64_t)48 << 30;
+  if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) budget = std::min<int64_t>(budget, (int64_t)(free_b / 2));
+  int64_t by_mem = std::max<int64_t>(1, budget / std::max<int64_t>(per_inst, 1));
+  return (int32_t)std::max<int64_t>(1, std::min<int64_t>({(int64_t)dawn::kMaxInstancesPerLaunch, by_tiles, by_mem}));
+}
+
+int ensure_workspace(dawn_graph g, int32_t k) {
+  if (g->ws_k >= k) return DAWN_OK;
+  free_workspace(g);
+  g->words = (g->n + 31) / 32;
+  g->tiles_cap = g->m / dawn::kTile + 2;
+  const size_t kn = (size_t)k * g->n;
+  int rc;
+  if ((rc = dalloc(&g->state, kn)) || (rc = dalloc(&g->bm0, (size_t)k * g->words)) ||
+      (rc = dalloc(&g->bm1, (size_t)k * g->words)) || (rc = dalloc(&g->q0, kn)) || (rc = dalloc(&g->q1, kn)) ||
+      (rc = dalloc(&g->t0, (size_t)k * g->tiles_cap)) || (rc = dalloc(&g->t1, (size_t)k * g->tiles_cap)) ||
+      (rc = dalloc(&g->tails, (size_t)3 * k))) {
+    free_workspace(g);
+    return rc;
+  }
+  g->ws_k = k;
+  return DAWN_OK;
+}
+
+int grid_for(dawn_graph g, int32_t k) {
+  const int is_f32 = g->wtype == DAWN_W_F32;
+  const int per_sm = std::max(1, dawn::govm_max_blocks_per_sm(is_f32));
+  const int cap = per_sm * g->sms;
+  if (g->grid_blocks > 0) return std::min(g->grid_blocks, cap);
+  // small problems get a small grid: barriers are cheaper with fewer blocks
+  const int64_t work = (int64_t)k * std::max<int64_t>(g->m, g->n);
+  const int64_t want = (work + 16383) / 16384;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(cap, want));
+}
+
+int run_solve(dawn_graph g, const int32_t *seeds, int32_t nseeds, int32_t source, int32_t k, int roots_mode,
+              void *dist, int32_t *parent, int32_t *parent_edge, cudaStream_t stream) {
+  int rc = ensure_workspace(g, k);
+  if (rc) return rc;
+  GovmParams p = {};
+  p.row_ptr = g->row_ptr;
+  p.col = g->col;
+  p.w = g->w;
+  p.src = g->src;
+  p.n = g->n;
+  p.m = g->m;
+  p.k = k;
+  p.roots_mode = roots_mode;
+  p.seeds = seeds;
+  p.nseeds = nseeds;
+  p.source = source;
+  p.state = g->state;
+  p.bitmap0 = g->bm0;
+  p.bitmap1 = g->bm1;
+  p.queue0 = g->q0;
+  p.queue1 = g->q1;
+  p.tiles0 = g->t0;
+  p.tiles1 = g->t1;
+  p.tails = g->tails;
+  p.words = g->words;
+  p.tiles_cap = g->tiles_cap;
+  p.dist = dist;
+  p.parent = parent;
+  p.parent_edge = parent_edge;
+  p.ctl = g->ctl;
+  p.max_steps = g->max_steps > 0 ? g->max_steps : g->n;
+  p.wait_limit_ns = g->wait_limit_ns;
+  p.test_stall = g->test_stall;
+  cudaError_t e = cudaMemsetAsync(g->ctl, 0, sizeof(DeviceCtl), stream);
+  if (e != cudaSuccess) return cuda_fail(e);
+  e = dawn::launch_govm(p, g->wtype == DAWN_W_F32, grid_for(g, k), stream);
+  if (e != cudaSuccess) return cuda_fail(e);
+  g->last_stream = stream;
+  return DAWN_OK;
+}
+
+int set_device(dawn_graph g) {
+  return cudaSetDevice(g->device) == cudaSuccess ? DAWN_OK : DAWN_ERR_CUDA;
+}
+
+int copy_in(void *dst, const void *src, size_t bytes, int on_device, cudaStream_t stream) {
+  if (bytes == 0) return DAWN_OK;
+  cudaError_t e = cudaMemcpyAsync(dst, src, bytes, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                  stream);
+  return e == cudaSuccess ? DAWN_OK : cuda_fail(e);
+}
+
+// Validates the device copy of the graph; synchronous.
+int validate(dawn_graph g, cudaStream_t stream) {
+  cudaError_t e = cudaMemsetAsync(g->vflags, 0, 2 * sizeof(unsigned), stream);
+  if (e != cudaSuccess) return cuda_fail(e);
+  const int64_t work = std::max<int64_t>(g->m, (int64_t)g->n + 1);
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((work + 255) / 256, (int64_t)g->sms * 8));
+  validate_kernel<<<blocks, 256, 0, stream>>>(g->row_ptr, g->col, g->w, g->n, g->m, g->wtype == DAWN_W_F32,
+                                               g->vflags);
+  unsigned h[2] = {0, 0};
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, g->vflags, sizeof(h), cudaMemcpyDeviceToHost, stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) return cuda_fail(e);
+  if (h[0]) return DAWN_ERR_INVALID;
+  // uint32: every candidate dist(u) + w is at most n * max(w) (shortest paths
+  // are simple); it must stay below the unreachable sentinel.
+  if (g->wtype == DAWN_W_U32 && (uint64_t)g->n * (uint64_t)h[1] >= 0xFFFFFFFFull) return DAWN_ERR_INVALID;
+  return DAWN_OK;
+}
+
+void release(dawn_graph g) {
+  free_workspace(g);
+  cudaFree(g->row_ptr);
+  cudaFree(g->col);
+  cudaFree(g->w);
+  cudaFree(g->src);
+  cudaFree(g->ctl);
+  cudaFree(g->vflags);
+  delete g;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *dawn_status_string(int code) {
+  switch (code) {
+    case DAWN_OK: return "DAWN_OK";
+    case DAWN_ERR_INVALID: return "DAWN_ERR_INVALID: invalid argument or graph";
+    case DAWN_ERR_OOM: return "DAWN_ERR_OOM: device allocation failed";
+    case DAWN_ERR_CUDA: return "DAWN_ERR_CUDA: CUDA runtime error";
+    case DAWN_ERR_NOT_CONVERGED: return "DAWN_ERR_NOT_CONVERGED: step cap reached";
+    case DAWN_ERR_TIMEOUT: return "DAWN_ERR_TIMEOUT: bounded in-kernel wait ran out";
+    case DAWN_ERR_BOUNDS: return "DAWN_ERR_BOUNDS: internal capacity check failed";
+    default: return "unknown dawn status";
+  }
+}
+
+int dawn_create_graph(int32_t n, int64_t m, const int32_t *row_ptr, const int32_t *col_idx, const void *weights,
+                      int wtype, int inputs_on_device, void *stream, dawn_graph *out) {
+  if (!out) return DAWN_ERR_INVALID;
+  *out = nullptr;
+  if (n < 1 || m < 0 || m > 0x7FFFFFFF || !row_ptr || (m > 0 && (!col_idx || !weights)) ||
+      (wtype != DAWN_W_U32 && wtype != DAWN_W_F32))
+    return DAWN_ERR_INVALID;
+  dawn_graph g = new (std::nothrow) dawn_graph_s();
+  if (!g) return DAWN_ERR_OOM;
+  g->n = n;
+  g->m = m;
+  g->wtype = wtype;
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = DAWN_OK;
+  if (cudaGetDevice(&g->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, g->device) != cudaSuccess) {
+    delete g;
+    return DAWN_ERR_CUDA;
+  }
+  if ((rc = dalloc(&g->row_ptr, (size_t)n + 1)) || (rc = dalloc(&g->col, (size_t)m)) || (rc = dalloc(&g->w, (size_t)m)) ||
+      (rc = dalloc(&g->src, (size_t)m)) || (rc = dalloc(&g->ctl, 1)) || (rc = dalloc(&g->vflags, 2)) ||
+      (rc = copy_in(g->row_ptr, row_ptr, ((size_t)n + 1) * 4, inputs_on_device, s)) ||
+      (rc = copy_in(g->col, col_idx, (size_t)m * 4, inputs_on_device, s)) ||
+      (rc = copy_in(g->w, weights, (size_t)m * 4, inputs_on_device, s)) || (rc = validate(g, s))) {
+    release(g);
+    return rc;
+  }
+  if (cudaMemsetAsync(g->ctl, 0, sizeof(DeviceCtl), s) != cudaSuccess) {
+    release(g);
+    return DAWN_ERR_CUDA;
+  }
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)n * 32 + 255) / 256, (int64_t)g->sms * 16));
+  edge_tail_kernel<<<blocks, 256, 0, s>>>(g->row_ptr, n, g->src);
+  if (cudaGetLastError() != cudaSuccess) {
+    release(g);
+    return DAWN_ERR_CUDA;
+  }
+  g->last_stream = s;
+  *out = g;
+  return DAWN_OK;
+}
+
+int dawn_set_weights(dawn_graph g, const void *weights, int inputs_on_device, void *stream) {
+  if (!g || (g->m > 0 && !weights)) return DAWN_ERR_INVALID;
+  if (set_device(g)) return DAWN_ERR_CUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = copy_in(g->w, weights, (size_t)g->m * 4, inputs_on_device, s);
+  if (rc) return rc;
+  g->last_stream = s;
+  return validate(g, s);
+}
+
+int dawn_reserve(dawn_graph g, int32_t k) {
+  if (!g || k < 1) return DAWN_ERR_INVALID;
+  if (set_device(g)) return DAWN_ERR_CUDA;
+  return ensure_workspace(g, std::min(k, max_chunk(g)));
+}
+
+int dawn_sssp(dawn_graph g, int32_t source, void *dist, int32_t *parent, int32_t *parent_edge, void *stream) {
+  if (!g || !dist || source < 0 || source >= g->n) return DAWN_ERR_INVALID;
+  if (set_device(g)) return DAWN_ERR_CUDA;
+  g->last_k = 1;
+  return run_solve(g, nullptr, 1, source, 1, 0, dist, parent, parent_edge, (cudaStream_t)stream);
+}
+
+int dawn_msssp(dawn_graph g, const int32_t *sources, int32_t k, void *dist, int32_t *parent, void *stream) {
+  if (!g || !sources || !dist || k < 1) return DAWN_ERR_INVALID;
+  if (set_device(g)) return DAWN_ERR_CUDA;
+  const int32_t chunk = std::min(k, g->ws_k > 0 ? std::max(g->ws_k, std::min(k, max_chunk(g))) : max_chunk(g));
+  g->last_k = k;
+  for (int32_t b = 0; b < k; b += chunk) {
+    const int32_t kk = std::min(chunk, k - b);
+    const size_t off = (size_t)b * g->n;
+    int rc = run_solve(g, sources + b, kk, 0, kk, 0, (uint32_t *)dist + off, parent ? parent + off : nullptr,
+                       nullptr, (cudaStream_t)stream);
+    if (rc) return rc;
+  }
+  return DAWN_OK;
+}
+
+int dawn_sssp_roots(dawn_graph g, const int32_t *roots, int32_t k, void *dist, int32_t *parent, int32_t *parent_edge,
+                    void *stream) {
+  if (!g || !roots || !dist || k < 1) return DAWN_ERR_INVALID;
+  if (set_device(g)) return DAWN_ERR_CUDA;
+  g->last_k = 1;
+  return run_solve(g, roots, k, 0, 1, 1, dist, parent, parent_edge, (cudaStream_t)stream);
+}
+
+int dawn_sssp_backward(dawn_graph g, const int32_t *parent_edge, const float *grad_dist, float *grad_w, void *stream) {
+  if (!g || !parent_edge || !grad_dist || (g->m > 0 && !grad_w)) return DAWN_ERR_INVALID;
+  if (g->wtype != DAWN_W_F32) return DAWN_ERR_INVALID;
+  if (set_device(g)) return DAWN_ERR_CUDA;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaMemsetAsync(g->ctl, 0, sizeof(DeviceCtl), s);
+  if (e != cudaSuccess) return cuda_fail(e);
+  if (g->m > 0) {
+    const int zb = (int)std::max<int64_t>(1, std::min<int64_t>((g->m + 255) / 256, (int64_t)g->sms * 8));
+    zero_f32_kernel<<<zb, 256, 0, s>>>(grad_w, g->m);
+    const int wb = (int)std::max<int64_t>(1, std::min<int64_t>((g->n + 255) / 256, (int64_t)g->sms * 8));
+    backward_walk_kernel<<<wb, 256, 0, s>>>(parent_edge, grad_dist, g->src, grad_w, g->n, g->m, g->ctl);
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e);
+  g->last_stream = s;
+  return DAWN_OK;
+}
+
+int dawn_status(dawn_graph g, int sync) {
+  if (!g) return DAWN_ERR_INVALID;
+  if (set_device(g)) return DAWN_ERR_CUDA;
+  if (sync && cudaStreamSynchronize(g->last_stream) != cudaSuccess) return DAWN_ERR_CUDA;
+  int st = 0;
+  if (cudaMemcpy(&st, &g->ctl->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return DAWN_ERR_CUDA;
+  return st;
+}
+
+int dawn_get_stats(dawn_graph g, dawn_stats *out) {
+  if (!g || !out) return DAWN_ERR_INVALID;
+  if (set_device(g)) return DAWN_ERR_CUDA;
+  if (cudaStreamSynchronize(g->last_stream) != cudaSuccess) return DAWN_ERR_CUDA;
+  DeviceCtl h;
+  if (cudaMemcpy(&h, g->ctl, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) return DAWN_ERR_CUDA;
+  out->steps = (int64_t)h.steps;
+  out->frontier_sum = (int64_t)h.frontier_sum;
+  out->edges_scanned = (int64_t)h.edges_scanned;
+  out->updates = (int64_t)h.updates;
+  out->instances = g->last_k;
+  return DAWN_OK;
+}
+
+int dawn_set_option(dawn_graph g, int option, int64_t value) {
+  if (!g) return DAWN_ERR_INVALID;
+  switch (option) {
+    case DAWN_OPT_MAX_STEPS: g->max_steps = value; return DAWN_OK;
+    case DAWN_OPT_WAIT_LIMIT_NS:
+      if (value <= 0) return DAWN_ERR_INVALID;
+      g->wait_limit_ns = (unsigned long long)value;
+      return DAWN_OK;
+    case DAWN_OPT_GRID_BLOCKS:
+      if (value < 0) return DAWN_ERR_INVALID;
+      g->grid_blocks = (int)value;
+      return DAWN_OK;
+    case DAWN_OPT_TEST_STALL: g->test_stall = value != 0; return DAWN_OK;
+    default: return DAWN_ERR_INVALID;
+  }
+}
+
+int dawn_graph_info(dawn_graph g, int32_t *n, int64_t *m, int *wtype) {
+  if (!g) return DAWN_ERR_INVALID;
+  if (n) *n = g->n;
+  if (m) *m = g->m;
+  if (wtype) *wtype = g->wtype;
+  return DAWN_OK;
+}
+
+void dawn_destroy(dawn_graph g) {
+  if (!g) return;
+  cudaSetDevice(g->device);
+  if (g->last_stream) cudaStreamSynchronize(g->last_stream);
+  release(g);
+}
+
+}  // extern "C"

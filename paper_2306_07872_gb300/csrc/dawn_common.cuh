@@ -1,0 +1,80 @@
+// Internal declarations shared by the CUDA translation units of libdawn.
+//
+// Data layout in device memory (one solver workspace per graph handle):
+//   state   u64 [k][n]   packed (key(dist) << 32) | parent edge.  key(d) is
+//                        d itself for uint32 weights and the IEEE bit pattern
+//                        for non-negative float32 weights; both are monotone
+//                        in d, so one 64-bit atomicMin updates the distance
+//                        and the parent edge together and keeps the
+//                        lexicographically smallest (dist, edge) pair.
+//   bitmap  u32 [2][k][words]   frontier membership (delta / beta of
+//                        Algorithm 2), one bit per vertex, double-buffered.
+//   queue   int2[2][k][n]  compacted frontier entries (vertex, offset of its
+//                        first out-edge in the frontier's virtual edge list).
+//   tiles   i32 [2][k][tiles_cap]  entry index that owns the first virtual
+//                        edge of every TILE-edge tile of the frontier.
+//   tails   u64 [3][k]   per-instance frontier size (low 32 bits) and total
+//                        out-degree (high 32 bits), updated by one atomicAdd
+//                        per warp so that entry order equals offset order.
+#pragma once
+
+#include <cstdint>
+
+#include "dawn.h"
+
+namespace dawn {
+
+constexpr int kTile = 256;           // virtual edges per warp task
+constexpr int kEdgesPerLane = kTile / 32;
+constexpr int kBlockThreads = 256;   // persistent kernel block size
+constexpr int kWarpsPerBlock = kBlockThreads / 32;
+constexpr int kMaxInstancesPerLaunch = 1024;  // per-block prefix over instances lives in shared memory
+constexpr uint32_t kNoEdge = 0xFFFFFFFFu;      // parent field of sources and unreachable vertices
+constexpr uint32_t kInfKeyU32 = 0xFFFFFFFFu;
+constexpr uint32_t kInfKeyF32 = 0x7F800000u;  // +inf
+
+// Control block: barrier, status and counters (zeroed before every launch).
+struct DeviceCtl {
+  unsigned int bar_count;
+  unsigned int bar_gen;
+  int status;
+  int stall_flag;  // never set by anyone: the test stall waits on it
+  unsigned long long steps;
+  unsigned long long frontier_sum;
+  unsigned long long edges_scanned;
+  unsigned long long updates;
+};
+
+struct GovmParams {
+  const int32_t *row_ptr;
+  const int32_t *col;
+  const uint32_t *w;        // weight bits (uint32 value or float32 bits)
+  const int32_t *src;       // tail of every edge
+  int32_t n;
+  int64_t m;
+  int32_t k;                // instances in this launch
+  int32_t roots_mode;       // 0: seeds[i] is the source of instance i; 1: all seeds root instance 0
+  const int32_t *seeds;      // device seeds, or null: then `source` is the only seed
+  int32_t nseeds;
+  int32_t source;
+  unsigned long long *state;
+  uint32_t *bitmap0, *bitmap1;
+  int2 *queue0, *queue1;
+  int32_t *tiles0, *tiles1;
+  unsigned long long *tails;  // [3][k]
+  int64_t words;             // bitmap words per instance
+  int64_t tiles_cap;         // tile slots per instance
+  void *dist;                // [k][n] u32 or f32 bits
+  int32_t *parent;           // [k][n] or null
+  int32_t *parent_edge;      // [k][n] or null
+  DeviceCtl *ctl;
+  int64_t max_steps;
+  unsigned long long wait_limit_ns;
+  int test_stall;
+};
+
+// Host-side launchers (govm_kernel.cu).
+cudaError_t launch_govm(const GovmParams &p, int is_f32, int grid_blocks, cudaStream_t stream);
+int govm_max_blocks_per_sm(int is_f32);
+
+}  // namespace dawn

@@ -1,0 +1,296 @@
+"""Thin Python binding of libdawn (include/dawn.h).
+
+The functions below carry the C entry points' names and only marshal
+arguments (torch tensors to device pointers, the current CUDA stream) and
+turn non-zero status codes into :class:`DawnError`.  Every step of the
+shortest-path computation runs in the CUDA kernels of libdawn.so; there is no
+CPU fallback, and importing this module without the built library fails.
+
+On top of the raw names sit two conveniences: :class:`Graph` (owns a handle
+and allocates output tensors) and :class:`DawnSSSP`, a
+``torch.autograd.Function`` whose forward is the GOVM solver and whose
+backward is the library's parent-tree scatter kernel.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdawn.so")
+
+DAWN_W_U32, DAWN_W_F32 = 0, 1
+DAWN_OK, DAWN_ERR_INVALID, DAWN_ERR_OOM, DAWN_ERR_CUDA = 0, 1, 2, 3
+DAWN_ERR_NOT_CONVERGED, DAWN_ERR_TIMEOUT, DAWN_ERR_BOUNDS = 4, 5, 6
+DAWN_OPT_MAX_STEPS, DAWN_OPT_WAIT_LIMIT_NS, DAWN_OPT_GRID_BLOCKS, DAWN_OPT_TEST_STALL = 1, 2, 3, 4
+
+EXPORTS = ("dawn_create_graph", "dawn_set_weights", "dawn_reserve", "dawn_sssp", "dawn_msssp", "dawn_sssp_roots",
+           "dawn_sssp_backward", "dawn_status", "dawn_get_stats", "dawn_set_option", "dawn_graph_info",
+           "dawn_status_string", "dawn_destroy")
+
+
+class DawnError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {status_string(code)}")
+
+
+class _Stats(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_int64) for f in ("steps", "frontier_sum", "edges_scanned", "updates", "instances")]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libdawn.so; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with paper_2306_07872_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    vp, i32, i64, c_int = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_int
+    sig = {
+        "dawn_create_graph": ([i32, i64, vp, vp, vp, c_int, c_int, vp, ctypes.POINTER(vp)], c_int),
+        "dawn_set_weights": ([vp, vp, c_int, vp], c_int),
+        "dawn_reserve": ([vp, i32], c_int),
+        "dawn_sssp": ([vp, i32, vp, vp, vp, vp], c_int),
+        "dawn_msssp": ([vp, vp, i32, vp, vp, vp], c_int),
+        "dawn_sssp_roots": ([vp, vp, i32, vp, vp, vp, vp], c_int),
+        "dawn_sssp_backward": ([vp, vp, vp, vp, vp], c_int),
+        "dawn_status": ([vp, c_int], c_int),
+        "dawn_get_stats": ([vp, ctypes.POINTER(_Stats)], c_int),
+        "dawn_set_option": ([vp, c_int, i64], c_int),
+        "dawn_graph_info": ([vp, ctypes.POINTER(i32), ctypes.POINTER(i64), ctypes.POINTER(c_int)], c_int),
+        "dawn_status_string": ([c_int], ctypes.c_char_p),
+        "dawn_destroy": ([vp], None),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def status_string(code: int) -> str:
+    return load_library().dawn_status_string(int(code)).decode()
+
+
+def _check(code: int, where: str):
+    if code != DAWN_OK:
+        raise DawnError(code, where)
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    if isinstance(stream, torch.cuda.Stream):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _dev(t: torch.Tensor | None, dtype=None, name="tensor") -> ctypes.c_void_p:
+    if t is None:
+        return ctypes.c_void_p(0)
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _any(t: torch.Tensor, dtype, name) -> tuple[ctypes.c_void_p, int]:
+    if t.dtype != dtype or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous {dtype} tensor")
+    return ctypes.c_void_p(t.data_ptr()), int(t.is_cuda)
+
+
+# ------------------------------------------------------------- raw entry points
+
+def dawn_create_graph(row_ptr: torch.Tensor, col_idx: torch.Tensor, weights: torch.Tensor, stream=None) -> int:
+    """Create a graph from CSR tensors (CPU or CUDA, int32 / int32 / uint32 or
+    float32); returns the opaque handle."""
+    lib = load_library()
+    n = row_ptr.numel() - 1
+    m = col_idx.numel()
+    if weights.dtype == torch.uint32:
+        wt = DAWN_W_U32
+    elif weights.dtype == torch.float32:
+        wt = DAWN_W_F32
+    else:
+        raise TypeError("weights must be torch.uint32 or torch.float32")
+    rp, on_dev = _any(row_ptr, torch.int32, "row_ptr")
+    cl, d2 = _any(col_idx, torch.int32, "col_idx")
+    w, d3 = _any(weights, weights.dtype, "weights")
+    if len({on_dev, d2, d3}) != 1:
+        raise ValueError("row_ptr, col_idx and weights must all be on the host or all on the device")
+    h = ctypes.c_void_p()
+    _check(lib.dawn_create_graph(n, m, rp, cl, w, wt, on_dev, _stream(stream), ctypes.byref(h)), "dawn_create_graph")
+    return h.value
+
+
+def dawn_set_weights(g: int, weights: torch.Tensor, stream=None):
+    w, on_dev = _any(weights, weights.dtype, "weights")
+    _check(load_library().dawn_set_weights(ctypes.c_void_p(g), w, on_dev, _stream(stream)), "dawn_set_weights")
+
+
+def dawn_reserve(g: int, k: int):
+    _check(load_library().dawn_reserve(ctypes.c_void_p(g), int(k)), "dawn_reserve")
+
+
+def dawn_sssp(g: int, source: int, dist: torch.Tensor, parent=None, parent_edge=None, stream=None):
+    _check(load_library().dawn_sssp(ctypes.c_void_p(g), int(source), _dev(dist, name="dist"),
+                                    _dev(parent, torch.int32, "parent"), _dev(parent_edge, torch.int32, "parent_edge"),
+                                    _stream(stream)), "dawn_sssp")
+
+
+def dawn_msssp(g: int, sources: torch.Tensor, dist: torch.Tensor, parent=None, stream=None):
+    _check(load_library().dawn_msssp(ctypes.c_void_p(g), _dev(sources, torch.int32, "sources"), sources.numel(),
+                                     _dev(dist, name="dist"), _dev(parent, torch.int32, "parent"), _stream(stream)),
+           "dawn_msssp")
+
+
+def dawn_sssp_roots(g: int, roots: torch.Tensor, dist: torch.Tensor, parent=None, parent_edge=None, stream=None):
+    _check(load_library().dawn_sssp_roots(ctypes.c_void_p(g), _dev(roots, torch.int32, "roots"), roots.numel(),
+                                          _dev(dist, name="dist"), _dev(parent, torch.int32, "parent"),
+                                          _dev(parent_edge, torch.int32, "parent_edge"), _stream(stream)),
+           "dawn_sssp_roots")
+
+
+def dawn_sssp_backward(g: int, parent_edge: torch.Tensor, grad_dist: torch.Tensor, grad_w: torch.Tensor, stream=None):
+    _check(load_library().dawn_sssp_backward(ctypes.c_void_p(g), _dev(parent_edge, torch.int32, "parent_edge"),
+                                             _dev(grad_dist, torch.float32, "grad_dist"),
+                                             _dev(grad_w, torch.float32, "grad_w"), _stream(stream)),
+           "dawn_sssp_backward")
+
+
+def dawn_status(g: int, sync: bool = True) -> int:
+    return int(load_library().dawn_status(ctypes.c_void_p(g), int(bool(sync))))
+
+
+def dawn_get_stats(g: int) -> dict:
+    st = _Stats()
+    _check(load_library().dawn_get_stats(ctypes.c_void_p(g), ctypes.byref(st)), "dawn_get_stats")
+    return {f: getattr(st, f) for f, _ in _Stats._fields_}
+
+
+def dawn_set_option(g: int, option: int, value: int):
+    _check(load_library().dawn_set_option(ctypes.c_void_p(g), int(option), int(value)), "dawn_set_option")
+
+
+def dawn_graph_info(g: int) -> tuple[int, int, int]:
+    n, m, wt = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int()
+    _check(load_library().dawn_graph_info(ctypes.c_void_p(g), ctypes.byref(n), ctypes.byref(m), ctypes.byref(wt)),
+           "dawn_graph_info")
+    return n.value, m.value, wt.value
+
+
+def dawn_status_string(code: int) -> str:
+    return status_string(code)
+
+
+def dawn_destroy(g: int):
+    if g:
+        load_library().dawn_destroy(ctypes.c_void_p(g))
+
+
+# ----------------------------------------------------------------- convenience
+
+class Graph:
+    """Owns a dawn graph handle; solves return freshly allocated tensors."""
+
+    def __init__(self, row_ptr, col_idx, weights, device="cuda", stream=None):
+        def t(x, dtype):
+            return x if isinstance(x, torch.Tensor) else torch.as_tensor(x, dtype=dtype)
+        row_ptr = t(row_ptr, torch.int32).contiguous()
+        col_idx = t(col_idx, torch.int32).contiguous()
+        weights = weights if isinstance(weights, torch.Tensor) else torch.from_numpy(weights)
+        weights = weights.contiguous()
+        self.device = torch.device(device)
+        with torch.cuda.device(self.device):
+            self.handle = dawn_create_graph(row_ptr, col_idx, weights, stream)
+        self.n, self.m, self.wtype = dawn_graph_info(self.handle)
+        self.dist_dtype = torch.uint32 if self.wtype == DAWN_W_U32 else torch.float32
+
+    def close(self):
+        if getattr(self, "handle", None):
+            dawn_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def check(self):
+        code = dawn_status(self.handle, True)
+        _check(code, "solve")
+
+    def sssp(self, source: int, parent: bool = True, parent_edge: bool = False, check: bool = True):
+        dist = torch.empty(self.n, dtype=self.dist_dtype, device=self.device)
+        par = torch.empty(self.n, dtype=torch.int32, device=self.device) if parent else None
+        pe = torch.empty(self.n, dtype=torch.int32, device=self.device) if parent_edge else None
+        dawn_sssp(self.handle, source, dist, par, pe)
+        if check:
+            self.check()
+        return dist, par, pe
+
+    def msssp(self, sources, parent: bool = True, check: bool = True):
+        src = torch.as_tensor(sources, dtype=torch.int32, device=self.device).contiguous()
+        k = src.numel()
+        dist = torch.empty((k, self.n), dtype=self.dist_dtype, device=self.device)
+        par = torch.empty((k, self.n), dtype=torch.int32, device=self.device) if parent else None
+        dawn_msssp(self.handle, src, dist, par)
+        if check:
+            self.check()
+        return dist, par
+
+    def sssp_roots(self, roots, parent: bool = True, parent_edge: bool = False, check: bool = True):
+        r = torch.as_tensor(roots, dtype=torch.int32, device=self.device).contiguous()
+        dist = torch.empty(self.n, dtype=self.dist_dtype, device=self.device)
+        par = torch.empty(self.n, dtype=torch.int32, device=self.device) if parent else None
+        pe = torch.empty(self.n, dtype=torch.int32, device=self.device) if parent_edge else None
+        dawn_sssp_roots(self.handle, r, dist, par, pe)
+        if check:
+            self.check()
+        return dist, par, pe
+
+    def stats(self) -> dict:
+        return dawn_get_stats(self.handle)
+
+    def set_option(self, option: int, value: int):
+        dawn_set_option(self.handle, option, value)
+
+
+class DawnSSSP(torch.autograd.Function):
+    """dist = DawnSSSP.apply(weights, graph, source).
+
+    Forward: loads `weights` (float32, one per CSR edge) into the graph and
+    runs the GOVM solver, saving only the parent tree.  Backward: the
+    library's kernel scatters dL/ddist along the parent tree, giving dL/dw
+    (the sum of dL/ddist over the subtree below each tree edge, 0 off the
+    tree)."""
+
+    @staticmethod
+    def forward(ctx, weights: torch.Tensor, graph: Graph, source: int):
+        if weights.dtype != torch.float32 or graph.wtype != DAWN_W_F32:
+            raise TypeError("DawnSSSP needs a float32 graph and float32 weights")
+        dawn_set_weights(graph.handle, weights.detach().contiguous())
+        dist, _, pe = graph.sssp(source, parent=False, parent_edge=True)
+        ctx.graph = graph
+        ctx.save_for_backward(pe)
+        ctx.mark_non_differentiable(pe)
+        return dist
+
+    @staticmethod
+    def backward(ctx, grad_dist):
+        (pe,) = ctx.saved_tensors
+        g = ctx.graph
+        grad_w = torch.empty(g.m, dtype=torch.float32, device=grad_dist.device)
+        dawn_sssp_backward(g.handle, pe, grad_dist.contiguous().float(), grad_w)
+        return grad_w, None, None

@@ -1,0 +1,75 @@
+"""CPU checks of the C-ABI boundary: the library builds, loads and exports
+every function declared in include/dawn.h; the Python binding carries the
+same names.  No compute call is made (no GPU here)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "dawn.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?(?:int|void|char\s*\*|const char\s*\*)\s*\*?\s*(dawn_\w+)\s*\(",
+                                 text, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def lib_path():
+    from paper_2306_07872_gb300 import build
+    try:
+        subprocess.run(["nvcc", "--version"], check=True, capture_output=True)
+    except (OSError, subprocess.CalledProcessError):
+        pytest.skip("nvcc not available")
+    return build.build()
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("dawn_create_graph", "dawn_sssp", "dawn_msssp", "dawn_destroy", "dawn_sssp_roots",
+                     "dawn_sssp_backward", "dawn_status"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib_path):
+    import torch  # noqa: F401  (puts the CUDA runtime on the loader path like the tests do)
+    lib = ctypes.CDLL(lib_path)
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+    out = subprocess.run(["nm", "-D", "--defined-only", lib_path], capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (dawn_\w+)", out))
+    assert set(declared_functions()) <= exported
+
+
+def test_binding_has_the_same_names(lib_path):
+    import paper_2306_07872_gb300 as pkg
+    for name in declared_functions():
+        assert hasattr(pkg.dawn, name), name
+    assert set(pkg.EXPORTS) == set(declared_functions())
+    assert pkg.dawn_status_string(5).startswith("DAWN_ERR_TIMEOUT")
+
+
+def test_binding_fails_loudly_without_library(tmp_path):
+    from paper_2306_07872_gb300 import dawn
+    saved = dawn._lib
+    dawn._lib = None
+    try:
+        with pytest.raises(ImportError):
+            dawn.load_library(str(tmp_path / "missing.so"))
+    finally:
+        dawn._lib = saved
+
+
+def test_oracle_is_not_imported_by_the_package():
+    pkg_dir = os.path.join(ROOT, "paper_2306_07872_gb300")
+    for dirpath, _, files in os.walk(pkg_dir):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in text and "from oracle" not in text, f
+                assert "graphgen" not in text, f

@@ -1,0 +1,90 @@
+"""GPU parity of the differentiable solver: the backward kernel's dL/dw
+against the oracle's float64 subtree-sum gradient and float64 central finite
+differences, with the parent tree as the only saved state.
+
+Tolerance: |g - g_ref| <= 1e-4 * max(|g_ref|, sum over the edge's subtree of
+|c_t|); the scale term covers fp32 atomic accumulation of many terms.
+"""
+import numpy as np
+import pytest
+import torch
+
+import graphgen as gg
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dawn():
+    import paper_2306_07872_gb300 as pkg
+    pkg.load_library()
+    return pkg
+
+
+def run_diff(dawn, wl):
+    g = dawn.Graph(wl.row_ptr, wl.col, wl.weights)
+    w = torch.from_numpy(wl.weights).cuda().requires_grad_(True)
+    dist = dawn.DawnSSSP.apply(w, g, 0)
+    tg = torch.from_numpy(wl.extra["targets"]).long().cuda()
+    cf = torch.from_numpy(wl.extra["coef"]).float().cuda()
+    loss = (dist[tg] * cf).sum()
+    loss.backward()
+    c = np.zeros(wl.n)
+    c[wl.extra["targets"]] = wl.extra["coef"].astype(np.float32).astype(np.float64)
+    return g, dist.detach().cpu().numpy(), w.grad.cpu().numpy(), c
+
+
+def subtree_abs(wl, pe, c):
+    return oracle.subtree_grad(wl.row_ptr, wl.col, wl.weights, 0, np.abs(c), parent_edge=pe)
+
+
+def test_backward_matches_reference_gradient(dawn):
+    wl = gg.rmat_f32_diff(scale=12, edge_factor=16, ntargets=128, seed=2)
+    g, dist, grad, c = run_diff(dawn, wl)
+    d_ref, _, pe_ref = oracle.sssp(wl.row_ptr, wl.col, wl.weights, 0)
+    assert np.array_equal(dist.view(np.uint32), d_ref.view(np.uint32))
+    g_ref = oracle.subtree_grad(wl.row_ptr, wl.col, wl.weights, 0, c, parent_edge=pe_ref)
+    scale = np.maximum(np.abs(g_ref), subtree_abs(wl, pe_ref, c))
+    assert np.all(np.abs(grad - g_ref) <= 1e-4 * scale + 1e-30)
+    assert np.all(grad[g_ref == 0] == 0)  # off-tree edges are exactly zero
+
+
+def test_backward_against_finite_differences(dawn):
+    wl = gg.rmat_f32_diff(scale=11, edge_factor=16, ntargets=64, seed=4)
+    g, dist, grad, c = run_diff(dawn, wl)
+    nz = np.nonzero(grad)[0]
+    pick = nz[gg.below(5, 0, 60, len(nz))]
+    fd, stable = oracle.fd_grad(wl.row_ptr, wl.col, wl.weights, 0, c, pick, h=1e-3)
+    assert stable.sum() >= 40
+    _, _, pe_ref = oracle.sssp(wl.row_ptr, wl.col, wl.weights, 0)
+    scale = np.maximum(np.abs(fd), subtree_abs(wl, pe_ref, c)[pick])
+    assert np.all(np.abs(grad[pick] - fd)[stable] <= 1e-4 * scale[stable])
+
+
+def test_backward_dense_grad_and_unreachable(dawn):
+    # dense dL/ddist including unreachable vertices (ignored) and the root
+    wl = gg.rmat_f32_diff(scale=10, edge_factor=4, ntargets=4, seed=3)
+    g = dawn.Graph(wl.row_ptr, wl.col, wl.weights)
+    dist, _, pe = g.sssp(0, parent=False, parent_edge=True)
+    cvec = torch.from_numpy(gg.uniform01(9, 0, wl.n).astype(np.float32) - 0.5).cuda()
+    grad_w = torch.empty(wl.m, dtype=torch.float32, device="cuda")
+    dawn.dawn_sssp_backward(g.handle, pe, cvec, grad_w)
+    g.check()
+    c = cvec.cpu().numpy().astype(np.float64)
+    fin = np.isfinite(dist.cpu().numpy())
+    c_eff = np.where(fin, c, 0.0)
+    pe_np = pe.cpu().numpy()
+    g_ref = oracle.subtree_grad(wl.row_ptr, wl.col, wl.weights, 0, c_eff, parent_edge=pe_np)
+    scale = np.maximum(np.abs(g_ref), subtree_abs(wl, pe_np, c_eff))
+    assert np.all(np.abs(grad_w.cpu().numpy() - g_ref) <= 1e-4 * scale + 1e-30)
+
+
+def test_backward_rejects_cyclic_parent_array(dawn):
+    rp, cl, w = gg.csr_from_edges(3, [(0, 1), (1, 2), (2, 1)], [1.0, 1.0, 1.0], np.float32)
+    g = dawn.Graph(rp, cl, w)
+    pe = torch.tensor([-1, 2, 1], dtype=torch.int32, device="cuda")  # 1 <- 2 <- 1
+    gd = torch.ones(3, dtype=torch.float32, device="cuda")
+    gw = torch.empty(3, dtype=torch.float32, device="cuda")
+    dawn.dawn_sssp_backward(g.handle, pe, gd, gw)
+    assert dawn.dawn_status(g.handle) == dawn.DAWN_ERR_INVALID
