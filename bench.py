@@ -110,8 +110,9 @@ class Clocks:
 
 def make_workload(name: str, rank: int = 0, world: int = 1):
     import graphgen as gg
-    if name == "rmat22":
-        wl = gg.rmat_u32(22, 16, nsrc=64 * world, seed=0)
+    if name.startswith("rmat") and name[4:].isdigit():
+        # rmat22 is the benchmark workload; smaller scales serve profiling
+        wl = gg.rmat_u32(int(name[4:]), 16, nsrc=64 * world, seed=0)
         wl.sources = wl.sources[rank * 64:(rank + 1) * 64]
         return wl
     if name == "grid":
@@ -188,7 +189,7 @@ def run_sssp_bench(args, wl, device, world, rank):
     mu = float(np.mean([st["updates"] for st in stats]))
     res = {
         "elapsed": elapsed,
-        "gteps": S * world * wl.e_wcc / elapsed / 1e9,
+        "gteps": S * args.steps * world * wl.e_wcc / elapsed / 1e9,
         "launch_ms_mean": float(launch_ms.mean()),
         "launch_ms_median": float(np.median(launch_ms)),
         "gteps_median": float(np.median(wl.e_wcc / (per_src_ms / 1e3) / 1e9)),
@@ -309,7 +310,8 @@ def main_reference(args):
     world, rank, local = dist_env()
     if rank != 0:
         return
-    wl = make_workload(args.workload if args.workload in ("rmat22", "grid", "tiny") else "rmat22")
+    wl = make_workload(args.workload if (args.workload.startswith("rmat") or args.workload in ("grid", "tiny"))
+                       else "rmat22")
     import oracle
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
     threads = max(1, min(cores, 16))
@@ -342,9 +344,11 @@ def main_ours(args):
     import torch
     if not torch.cuda.is_available():
         raise SystemExit("bench.py needs a CUDA GPU (the solver has no CPU path)")
-    if args.workload in ("rmat22", "grid", "tiny"):
+    if args.workload.startswith("rmat") or args.workload in ("grid", "tiny"):
         t = time.time()
         wl = make_workload(args.workload, rank, world)
+        if args.sources:
+            wl.sources = wl.sources[:args.sources]
         log(f"[bench] {wl.name}: n={wl.n} m={wl.m} e_wcc={wl.e_wcc} sources={len(wl.sources)} "
             f"(generated in {time.time() - t:.1f} s)")
         res = run_sssp_bench(args, wl, device, world, rank)
@@ -389,6 +393,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--sources", type=int, default=0, help="limit sources per step (profiling runs)")
     args = ap.parse_args()
     if args.warmup < 3:
         log("[bench] warm-up raised to 3 steps")
