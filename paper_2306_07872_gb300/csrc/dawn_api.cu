@@ -38,6 +38,7 @@ struct dawn_graph_s {
   unsigned long long wait_limit_ns = 4000000000ull;
   int grid_blocks = 0;
   int test_stall = 0;
+  int blocks_per_sm = 0;  // co-resident persistent blocks per SM (cached)
   int last_k = 0;
   cudaStream_t last_stream = nullptr;
 };
@@ -193,8 +194,8 @@ int ensure_workspace(dawn_graph g, int32_t k) {
 }
 
 int grid_for(dawn_graph g, int32_t k) {
-  const int is_f32 = g->wtype == DAWN_W_F32;
-  const int per_sm = std::max(1, dawn::govm_max_blocks_per_sm(is_f32));
+  if (g->blocks_per_sm == 0) g->blocks_per_sm = std::max(1, dawn::govm_max_blocks_per_sm(g->wtype == DAWN_W_F32));
+  const int per_sm = g->blocks_per_sm;
   const int cap = per_sm * g->sms;
   if (g->grid_blocks > 0) return std::min(g->grid_blocks, cap);
   // small problems get a small grid: barriers are cheaper with fewer blocks

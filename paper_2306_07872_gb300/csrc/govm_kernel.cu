@@ -65,11 +65,15 @@ struct Key<true> {
   }
 };
 
+constexpr int kStage = 2 * kTile;  // staged entries per warp (flushed above kStage - kTile)
+
 struct WarpTile {
   int32_t rs[kTile + 1];     // CSR row start of each entry of the tile
   uint32_t off[kTile + 1];   // virtual offset of each entry's first edge
   uint32_t dkey[kTile + 1];  // distance key of each entry's vertex (read at expansion time)
   int32_t own[kTile];        // owning entry (relative index) of every virtual edge
+  int32_t bv[kStage];        // staged next-frontier vertices
+  uint32_t bd[kStage];       // and their out-degrees
 };
 
 struct BlockShared {
@@ -172,62 +176,93 @@ __device__ __forceinline__ int32_t find_instance(const int32_t *tprefix, int32_t
   return lo;
 }
 
-// Warp-aggregated append of the lanes' pending entries (bit r of `mask`:
-// vertex tgt[r] with out-degree dg[r]) to instance `inst`'s next queue.  One
-// atomicAdd on the packed tail (count | degree-sum << 32) reserves a block of
-// entries and the matching block of virtual edges; the tile table of the next
-// frontier records which entry owns each tile's first edge.
-__device__ __forceinline__ void warp_append(const GovmParams &p, int32_t inst, int nxt, unsigned long long *tails_next,
-                                            unsigned mask, const int32_t (&tgt)[kEdgesPerLane],
-                                            const uint32_t (&dg)[kEdgesPerLane]) {
+// Next-frontier entries found by a warp are staged in its shared-memory
+// buffer (vertex, out-degree) and appended to the instance's queue in bulk:
+// one atomicAdd on the packed tail (count | degree-sum << 32) per flush
+// reserves a block of entries and the matching block of virtual edges, so the
+// queue order equals the offset order.  Staging across tiles keeps the number
+// of atomics on the (single, hot) tail word low.
+
+// Stage the lanes' pending entries (bit r of mask: vertex tgt[r], out-degree
+// dg[r]); `count` is the warp-uniform number of staged entries.
+__device__ __forceinline__ void stage_entries(WarpTile &wt, int &count, unsigned mask,
+                                              const int32_t (&tgt)[kEdgesPerLane],
+                                              const uint32_t (&dg)[kEdgesPerLane]) {
   const int lane = threadIdx.x & 31;
-  uint32_t cnt = __popc(mask), degsum = 0;
-#pragma unroll
-  for (int r = 0; r < kEdgesPerLane; ++r)
-    if (mask & (1u << r)) degsum += dg[r];
-  unsigned long long mine = ((unsigned long long)degsum << 32) | cnt;
-  unsigned long long incl = mine;
+  const int mine = __popc(mask);
+  int incl = mine;
 #pragma unroll
   for (int d = 1; d < 32; d <<= 1) {
-    unsigned long long o = __shfl_up_sync(kFull, incl, d);
+    int o = __shfl_up_sync(kFull, incl, d);
     if (lane >= d) incl += o;
   }
-  unsigned long long total = __shfl_sync(kFull, incl, 31);
-  if (total == 0) return;
-  unsigned long long base = 0;
-  if (lane == 31) base = atomicAdd(tails_next + inst, total);
-  base = __shfl_sync(kFull, base, 31);
-  unsigned long long pos = base + (incl - mine);
-  uint32_t idx = (uint32_t)pos;
-  uint32_t off = (uint32_t)(pos >> 32);
-  int2 *q = (nxt ? p.queue1 : p.queue0) + (size_t)inst * p.n;
-  int32_t *tl = (nxt ? p.tiles1 : p.tiles0) + (size_t)inst * p.tiles_cap;
+  int pos = count + incl - mine;
 #pragma unroll
   for (int r = 0; r < kEdgesPerLane; ++r) {
-    if (!(mask & (1u << r))) continue;
-    if (idx >= (uint32_t)p.n) {  // cannot happen: the bitmap admits a vertex once per step
-      set_status(p.ctl, DAWN_ERR_BOUNDS);
-      return;
+    if (mask & (1u << r)) {
+      wt.bv[pos] = tgt[r];
+      wt.bd[pos] = dg[r];
+      ++pos;
     }
-    q[idx] = make_int2(tgt[r], (int32_t)off);
-    uint32_t end = off + dg[r];
-    for (uint32_t tb = (off + kTile - 1) / kTile; tb * (uint32_t)kTile < end; ++tb) {
-      if (tb >= (uint32_t)p.tiles_cap) {
-        set_status(p.ctl, DAWN_ERR_BOUNDS);
-        return;
-      }
-      tl[tb] = (int32_t)idx;
-    }
-    ++idx;
-    off = end;
   }
+  count += __shfl_sync(kFull, incl, 31);
+  __syncwarp();
+}
+
+// Append the staged entries to instance inst's queue `nxt` and record, in the
+// next frontier's tile table, which entry owns the first edge of each tile.
+__device__ void flush_entries(const GovmParams &p, WarpTile &wt, int &count, int32_t inst, int nxt,
+                              unsigned long long *tails_next) {
+  const int lane = threadIdx.x & 31;
+  if (count == 0) return;
+  unsigned long long degsum = 0;
+  for (int i = lane; i < count; i += 32) degsum += wt.bd[i];
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) degsum += __shfl_xor_sync(kFull, degsum, d);
+  unsigned long long base = 0;
+  if (lane == 0) base = atomicAdd(tails_next + inst, (degsum << 32) | (unsigned long long)count);
+  base = __shfl_sync(kFull, base, 0);
+  const uint32_t idx0 = (uint32_t)base;
+  uint32_t run = (uint32_t)(base >> 32);
+  int2 *q = (nxt ? p.queue1 : p.queue0) + (size_t)inst * p.n;
+  int32_t *tl = (nxt ? p.tiles1 : p.tiles0) + (size_t)inst * p.tiles_cap;
+  for (int b = 0; b < count; b += 32) {
+    const int i = b + lane;
+    const uint32_t d = i < count ? wt.bd[i] : 0u;
+    uint32_t incl = d;
+#pragma unroll
+    for (int s = 1; s < 32; s <<= 1) {
+      uint32_t o = __shfl_up_sync(kFull, incl, s);
+      if (lane >= s) incl += o;
+    }
+    if (i < count) {
+      const uint32_t idx = idx0 + (uint32_t)i;
+      const uint32_t off = run + incl - d;
+      if (idx >= (uint32_t)p.n) {  // cannot happen: the bitmap admits a vertex once per step
+        set_status(p.ctl, DAWN_ERR_BOUNDS);
+      } else {
+        q[idx] = make_int2(wt.bv[i], (int32_t)off);
+        const uint32_t end = off + d;
+        for (uint32_t tb = (off + kTile - 1) / kTile; tb * (uint32_t)kTile < end; ++tb) {
+          if (tb >= (uint32_t)p.tiles_cap) {
+            set_status(p.ctl, DAWN_ERR_BOUNDS);
+            break;
+          }
+          tl[tb] = (int32_t)idx;
+        }
+      }
+    }
+    run += __shfl_sync(kFull, incl, 31);
+  }
+  count = 0;
+  __syncwarp();
 }
 
 // Relax the out-edges in virtual-edge tile t of instance inst's frontier.
 template <bool F32>
 __device__ __forceinline__ void process_tile(const GovmParams &p, WarpTile &wt, int32_t inst, int32_t t,
                                              unsigned long long tail_cur, int32_t tiles_i, int cur,
-                                             unsigned long long *tails_next, unsigned long long &updates) {
+                                             int &staged, unsigned long long &updates) {
   const int lane = threadIdx.x & 31;
   const uint32_t E = (uint32_t)(tail_cur >> 32);
   const int32_t c = (int32_t)(uint32_t)tail_cur;
@@ -356,12 +391,13 @@ __device__ __forceinline__ void process_tile(const GovmParams &p, WarpTile &wt, 
 #pragma unroll
   for (int r = 0; r < kEdgesPerLane; ++r)
     if ((mark & (1u << r)) && !(obits[r] & (1u << (tgt[r] & 31)))) mask |= 1u << r;
-  warp_append(p, inst, cur ^ 1, tails_next, mask, tgt, dg);
+  stage_entries(wt, staged, mask, tgt, dg);
 }
 
 template <bool F32>
 __global__ void __launch_bounds__(kBlockThreads) govm_kernel(GovmParams p) {
-  __shared__ BlockShared sh;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  BlockShared &sh = *reinterpret_cast<BlockShared *>(smem_raw);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const long long gtid = (long long)blockIdx.x * blockDim.x + tid;
   const long long gsize = (long long)gridDim.x * blockDim.x;
@@ -423,6 +459,7 @@ __global__ void __launch_bounds__(kBlockThreads) govm_kernel(GovmParams p) {
     if (!grid_barrier(ctl, p.wait_limit_ns, &sh.flag)) goto finish;
     // warp-uniform loop: every lane of a warp takes part in the append
     const long long gw = gtid >> 5, nw = gsize >> 5;
+    int staged = 0;
     for (long long b = gw * 32; b < p.nseeds; b += nw * 32) {
       const long long i = b + lane;
       int32_t tg[kEdgesPerLane] = {0};
@@ -442,8 +479,10 @@ __global__ void __launch_bounds__(kBlockThreads) govm_kernel(GovmParams p) {
           }
         }
       }
-      warp_append(p, 0, 0, p.tails, mask, tg, dgs);
+      stage_entries(sh.wt[warp], staged, mask, tg, dgs);
+      if (staged > kStage - 32) flush_entries(p, sh.wt[warp], staged, 0, 0, p.tails);
     }
+    flush_entries(p, sh.wt[warp], staged, 0, 0, p.tails);
   }
   if (!grid_barrier(ctl, p.wait_limit_ns, &sh.flag)) goto finish;
 
@@ -476,12 +515,18 @@ __global__ void __launch_bounds__(kBlockThreads) govm_kernel(GovmParams p) {
     }
     const int32_t gw = blockIdx.x * kWarpsPerBlock + warp;
     const int32_t nw = gridDim.x * kWarpsPerBlock;
+    int staged = 0;
+    int32_t staged_inst = 0;
     for (int32_t g = gw; g < total_tiles; g += nw) {
       const int32_t inst = find_instance(sh.tprefix, p.k, g);
       const int32_t t = g - sh.tprefix[inst];
       const int32_t tiles_i = sh.tprefix[inst + 1] - sh.tprefix[inst];
-      process_tile<F32>(p, sh.wt[warp], inst, t, __ldcg(tails_cur + inst), tiles_i, cur, tails_next, updates);
+      if (staged > 0 && inst != staged_inst) flush_entries(p, sh.wt[warp], staged, staged_inst, cur ^ 1, tails_next);
+      staged_inst = inst;
+      process_tile<F32>(p, sh.wt[warp], inst, t, __ldcg(tails_cur + inst), tiles_i, cur, staged, updates);
+      if (staged > kStage - kTile) flush_entries(p, sh.wt[warp], staged, inst, cur ^ 1, tails_next);
     }
+    flush_entries(p, sh.wt[warp], staged, staged_inst, cur ^ 1, tails_next);
     if (!grid_barrier(ctl, p.wait_limit_ns, &sh.flag)) break;
   }
 
@@ -518,11 +563,25 @@ finish:
 
 }  // namespace
 
+// Shared memory exceeds the 48 KB static limit: opt in once per kernel.
+cudaError_t prepare_kernels() {
+  static bool done = false;
+  if (done) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(govm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sizeof(BlockShared));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(govm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(BlockShared));
+  done = e == cudaSuccess;
+  return e;
+}
+
 cudaError_t launch_govm(const GovmParams &p, int is_f32, int grid_blocks, cudaStream_t stream) {
+  cudaError_t e = prepare_kernels();
+  if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)grid_blocks);
   cfg.blockDim = dim3(kBlockThreads);
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = sizeof(BlockShared);
   cfg.stream = stream;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;
@@ -535,8 +594,10 @@ cudaError_t launch_govm(const GovmParams &p, int is_f32, int grid_blocks, cudaSt
 
 int govm_max_blocks_per_sm(int is_f32) {
   int nb = 0;
-  cudaError_t e = is_f32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, govm_kernel<true>, kBlockThreads, 0)
-                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, govm_kernel<false>, kBlockThreads, 0);
+  if (prepare_kernels() != cudaSuccess) return 0;
+  const size_t smem = sizeof(BlockShared);
+  cudaError_t e = is_f32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, govm_kernel<true>, kBlockThreads, smem)
+                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, govm_kernel<false>, kBlockThreads, smem);
   return e == cudaSuccess ? nb : 0;
 }
 
