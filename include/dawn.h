@@ -177,9 +177,27 @@ int dawn_get_stats(dawn_graph g, dawn_stats *out);
  *   DAWN_OPT_GRID_BLOCKS   persistent grid size (0 = all co-resident blocks)
  *   DAWN_OPT_TEST_STALL    1: block 0 waits on a flag nothing sets, so the
  *                          bounded waits run out (tests DAWN_ERR_TIMEOUT)
+ *   DAWN_OPT_TRACE_STEPS   record up to `value` per-step trace rows in later
+ *                          solves (0 = off, the default); allocates
  */
-enum { DAWN_OPT_MAX_STEPS = 1, DAWN_OPT_WAIT_LIMIT_NS = 2, DAWN_OPT_GRID_BLOCKS = 3, DAWN_OPT_TEST_STALL = 4 };
+enum {
+  DAWN_OPT_MAX_STEPS = 1,
+  DAWN_OPT_WAIT_LIMIT_NS = 2,
+  DAWN_OPT_GRID_BLOCKS = 3,
+  DAWN_OPT_TEST_STALL = 4,
+  DAWN_OPT_TRACE_STEPS = 5
+};
 int dawn_set_option(dawn_graph g, int option, int64_t value);
+
+/*
+ * Per-step trace of the last solve (enable with DAWN_OPT_TRACE_STEPS; waits
+ * for the solve).  Row i (4 int64 values): device time in ns when step i
+ * started (the last row: when the iteration ended), the cumulative frontier
+ * size |delta| and cumulative frontier out-edges before step i, and a flag
+ * that is 1 on the last row.  Returns the number of rows written (at most
+ * cap), 0 when tracing is off, or a negated status code.
+ */
+int dawn_get_trace(dawn_graph g, int64_t *out, int32_t cap);
 
 /* Basic graph facts: n, m and the weight type. */
 int dawn_graph_info(dawn_graph g, int32_t *n, int64_t *m, int *wtype);

@@ -20,9 +20,12 @@ struct dawn_graph_s {
   int device = 0;
   int sms = 0;
   int32_t *row_ptr = nullptr;
-  int32_t *col = nullptr;
-  uint32_t *w = nullptr;
+  int32_t *col = nullptr;   // staging copy of the columns (freed after interleaving)
+  uint32_t *w = nullptr;    // weight bits as given (kept for dawn_set_weights)
+  uint2 *cw = nullptr;      // (column, weight bits) per edge: the array the solver streams
   int32_t *src = nullptr;
+  unsigned long long *trace = nullptr;
+  int32_t trace_cap = 0;
   // solver workspace for up to ws_k instances
   int32_t ws_k = 0;
   unsigned long long *state = nullptr;
@@ -59,8 +62,10 @@ __global__ void validate_kernel(const int32_t *row_ptr, const int32_t *col, cons
     if (v < n && row_ptr[v + 1] < r) bad |= kBadRowPtr;
   }
   for (long long e = gtid; e < m; e += gsize) {
-    const int32_t c = col[e];
-    if (c < 0 || c >= n) bad |= kBadCol;
+    if (col) {
+      const int32_t c = col[e];
+      if (c < 0 || c >= n) bad |= kBadCol;
+    }
     const uint32_t x = w[e];
     if (is_f32) {
       const float f = __uint_as_float(x);
@@ -87,6 +92,16 @@ __global__ void edge_tail_kernel(const int32_t *row_ptr, int32_t n, int32_t *src
   for (long long u = warp; u < n; u += nwarps) {
     const int32_t b = row_ptr[u], e = row_ptr[u + 1];
     for (int32_t i = b + lane; i < e; i += 32) src[i] = (int32_t)u;
+  }
+}
+
+// cw[e] = (col[e], w[e]); with col == null only the weight half is rewritten.
+__global__ void interleave_kernel(const int32_t *col, const uint32_t *w, int64_t m, uint2 *cw) {
+  const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long gsize = (long long)gridDim.x * blockDim.x;
+  for (long long e = gtid; e < m; e += gsize) {
+    if (col) cw[e] = make_uint2((uint32_t)col[e], w[e]);
+    else cw[e].y = w[e];
   }
 }
 
@@ -210,8 +225,7 @@ int run_solve(dawn_graph g, const int32_t *seeds, int32_t nseeds, int32_t source
   if (rc) return rc;
   GovmParams p = {};
   p.row_ptr = g->row_ptr;
-  p.col = g->col;
-  p.w = g->w;
+  p.cw = g->cw;
   p.src = g->src;
   p.n = g->n;
   p.m = g->m;
@@ -237,7 +251,11 @@ int run_solve(dawn_graph g, const int32_t *seeds, int32_t nseeds, int32_t source
   p.max_steps = g->max_steps > 0 ? g->max_steps : g->n;
   p.wait_limit_ns = g->wait_limit_ns;
   p.test_stall = g->test_stall;
+  p.trace = g->trace;
+  p.trace_cap = g->trace_cap;
   cudaError_t e = cudaMemsetAsync(g->ctl, 0, sizeof(DeviceCtl), stream);
+  if (e == cudaSuccess && g->trace)
+    e = cudaMemsetAsync(g->trace, 0, (size_t)g->trace_cap * 4 * sizeof(unsigned long long), stream);
   if (e != cudaSuccess) return cuda_fail(e);
   e = dawn::launch_govm(p, g->wtype == DAWN_W_F32, grid_for(g, k), stream);
   if (e != cudaSuccess) return cuda_fail(e);
@@ -281,6 +299,8 @@ void release(dawn_graph g) {
   cudaFree(g->row_ptr);
   cudaFree(g->col);
   cudaFree(g->w);
+  cudaFree(g->cw);
+  cudaFree(g->trace);
   cudaFree(g->src);
   cudaFree(g->ctl);
   cudaFree(g->vflags);
@@ -324,6 +344,7 @@ int dawn_create_graph(int32_t n, int64_t m, const int32_t *row_ptr, const int32_
     return DAWN_ERR_CUDA;
   }
   if ((rc = dalloc(&g->row_ptr, (size_t)n + 1)) || (rc = dalloc(&g->col, (size_t)m)) || (rc = dalloc(&g->w, (size_t)m)) ||
+      (rc = dalloc(&g->cw, (size_t)m)) ||
       (rc = dalloc(&g->src, (size_t)m)) || (rc = dalloc(&g->ctl, 1)) || (rc = dalloc(&g->vflags, 2)) ||
       (rc = copy_in(g->row_ptr, row_ptr, ((size_t)n + 1) * 4, inputs_on_device, s)) ||
       (rc = copy_in(g->col, col_idx, (size_t)m * 4, inputs_on_device, s)) ||
@@ -337,10 +358,14 @@ int dawn_create_graph(int32_t n, int64_t m, const int32_t *row_ptr, const int32_
   }
   const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)n * 32 + 255) / 256, (int64_t)g->sms * 16));
   edge_tail_kernel<<<blocks, 256, 0, s>>>(g->row_ptr, n, g->src);
-  if (cudaGetLastError() != cudaSuccess) {
+  const int eb = (int)std::max<int64_t>(1, std::min<int64_t>((m + 255) / 256, (int64_t)g->sms * 16));
+  interleave_kernel<<<eb, 256, 0, s>>>(g->col, g->w, m, g->cw);
+  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
     release(g);
     return DAWN_ERR_CUDA;
   }
+  cudaFree(g->col);  // columns now live in cw
+  g->col = nullptr;
   g->last_stream = s;
   *out = g;
   return DAWN_OK;
@@ -353,7 +378,13 @@ int dawn_set_weights(dawn_graph g, const void *weights, int inputs_on_device, vo
   int rc = copy_in(g->w, weights, (size_t)g->m * 4, inputs_on_device, s);
   if (rc) return rc;
   g->last_stream = s;
-  return validate(g, s);
+  if ((rc = validate(g, s))) return rc;
+  if (g->m > 0) {
+    const int eb = (int)std::max<int64_t>(1, std::min<int64_t>((g->m + 255) / 256, (int64_t)g->sms * 16));
+    interleave_kernel<<<eb, 256, 0, s>>>(nullptr, g->w, g->m, g->cw);
+    if (cudaGetLastError() != cudaSuccess) return DAWN_ERR_CUDA;
+  }
+  return DAWN_OK;
 }
 
 int dawn_reserve(dawn_graph g, int32_t k) {
@@ -447,8 +478,40 @@ int dawn_set_option(dawn_graph g, int option, int64_t value) {
       g->grid_blocks = (int)value;
       return DAWN_OK;
     case DAWN_OPT_TEST_STALL: g->test_stall = value != 0; return DAWN_OK;
+    case DAWN_OPT_TRACE_STEPS: {
+      if (value < 0 || value > (1 << 24)) return DAWN_ERR_INVALID;
+      if (set_device(g)) return DAWN_ERR_CUDA;
+      if (g->last_stream) cudaStreamSynchronize(g->last_stream);
+      cudaFree(g->trace);
+      g->trace = nullptr;
+      g->trace_cap = 0;
+      if (value == 0) return DAWN_OK;
+      int rc = dalloc(&g->trace, (size_t)value * 4);
+      if (rc) return rc;
+      if (cudaMemset(g->trace, 0, (size_t)value * 4 * sizeof(unsigned long long)) != cudaSuccess) return DAWN_ERR_CUDA;
+      g->trace_cap = (int32_t)value;
+      return DAWN_OK;
+    }
     default: return DAWN_ERR_INVALID;
   }
+}
+
+int dawn_get_trace(dawn_graph g, int64_t *out, int32_t cap) {
+  if (!g || !out || cap < 0) return -DAWN_ERR_INVALID;
+  if (!g->trace) return 0;
+  if (set_device(g)) return -DAWN_ERR_CUDA;
+  if (cudaStreamSynchronize(g->last_stream) != cudaSuccess) return -DAWN_ERR_CUDA;
+  const int32_t rows = std::min(cap, g->trace_cap);
+  if (rows == 0) return 0;
+  if (cudaMemcpy(out, g->trace, (size_t)rows * 4 * sizeof(int64_t), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return -DAWN_ERR_CUDA;
+  int32_t used = 0;
+  while (used < rows && out[4 * used] != 0) {
+    const bool last = out[4 * used + 3] == 1;
+    ++used;
+    if (last) break;
+  }
+  return used;
 }
 
 int dawn_graph_info(dawn_graph g, int32_t *n, int64_t *m, int *wtype) {

@@ -13,6 +13,7 @@
 //                        first out-edge in the frontier's virtual edge list).
 //   tiles   i32 [2][k][tiles_cap]  entry index that owns the first virtual
 //                        edge of every TILE-edge tile of the frontier.
+//   cw      uint2[m]     the CSR column and weight of every edge, interleaved.
 //   tails   u64 [3][k]   per-instance frontier size (low 32 bits) and total
 //                        out-degree (high 32 bits), updated by one atomicAdd
 //                        per warp so that entry order equals offset order.
@@ -47,8 +48,7 @@ struct DeviceCtl {
 
 struct GovmParams {
   const int32_t *row_ptr;
-  const int32_t *col;
-  const uint32_t *w;        // weight bits (uint32 value or float32 bits)
+  const uint2 *cw;          // per edge: (column, weight bits), interleaved for one 8-byte load
   const int32_t *src;       // tail of every edge
   int32_t n;
   int64_t m;
@@ -71,6 +71,8 @@ struct GovmParams {
   int64_t max_steps;
   unsigned long long wait_limit_ns;
   int test_stall;
+  unsigned long long *trace;  // optional per-step trace [trace_cap][4], null when off
+  int32_t trace_cap;
 };
 
 // Host-side launchers (govm_kernel.cu).

@@ -347,8 +347,9 @@ __device__ __forceinline__ void process_tile(const GovmParams &p, WarpTile &wt, 
       }
       valid |= 1u << r;
       eidx[r] = e;
-      tgt[r] = __ldcs(p.col + e);
-      ckey[r] = Key<F32>::add(wt.dkey[j], __ldcs(p.w + e));
+      const uint2 cw = __ldcs(p.cw + e);
+      tgt[r] = (int32_t)cw.x;
+      ckey[r] = Key<F32>::add(wt.dkey[j], cw.y);
     }
   }
   unsigned long long curst[kEdgesPerLane];
@@ -503,6 +504,14 @@ __global__ void __launch_bounds__(kBlockThreads) govm_kernel(GovmParams p) {
       break;
     }
     if (blockIdx.x == 0) {
+      if (tid == 0 && p.trace && step < p.trace_cap) {
+        unsigned long long *tr = p.trace + 4 * step;
+        tr[0] = global_ns();
+        tr[1] = __ldcg(&ctl->frontier_sum);  // cumulative before this step
+        tr[2] = __ldcg(&ctl->edges_scanned);
+        tr[3] = 0;
+      }
+      __syncthreads();
       unsigned long long fs = 0, es = 0;
       for (int32_t i = tid; i < p.k; i += blockDim.x) {
         const unsigned long long tl = __ldcg(tails_cur + i);
@@ -528,6 +537,14 @@ __global__ void __launch_bounds__(kBlockThreads) govm_kernel(GovmParams p) {
     }
     flush_entries(p, sh.wt[warp], staged, staged_inst, cur ^ 1, tails_next);
     if (!grid_barrier(ctl, p.wait_limit_ns, &sh.flag)) break;
+  }
+
+  if (quiescent && blockIdx.x == 0 && tid == 0 && p.trace && step < p.trace_cap) {
+    unsigned long long *tr = p.trace + 4 * step;
+    tr[0] = global_ns();
+    tr[1] = __ldcg(&ctl->frontier_sum);
+    tr[2] = __ldcg(&ctl->edges_scanned);
+    tr[3] = 1;  // final row
   }
 
   // 4. Outputs (only from a quiescent state: every block left the loop at the

@@ -25,9 +25,10 @@ DAWN_W_U32, DAWN_W_F32 = 0, 1
 DAWN_OK, DAWN_ERR_INVALID, DAWN_ERR_OOM, DAWN_ERR_CUDA = 0, 1, 2, 3
 DAWN_ERR_NOT_CONVERGED, DAWN_ERR_TIMEOUT, DAWN_ERR_BOUNDS = 4, 5, 6
 DAWN_OPT_MAX_STEPS, DAWN_OPT_WAIT_LIMIT_NS, DAWN_OPT_GRID_BLOCKS, DAWN_OPT_TEST_STALL = 1, 2, 3, 4
+DAWN_OPT_TRACE_STEPS = 5
 
 EXPORTS = ("dawn_create_graph", "dawn_set_weights", "dawn_reserve", "dawn_sssp", "dawn_msssp", "dawn_sssp_roots",
-           "dawn_sssp_backward", "dawn_status", "dawn_get_stats", "dawn_set_option", "dawn_graph_info",
+           "dawn_sssp_backward", "dawn_status", "dawn_get_stats", "dawn_set_option", "dawn_get_trace", "dawn_graph_info",
            "dawn_status_string", "dawn_destroy")
 
 
@@ -64,6 +65,7 @@ def load_library(path: str = LIB_PATH):
         "dawn_status": ([vp, c_int], c_int),
         "dawn_get_stats": ([vp, ctypes.POINTER(_Stats)], c_int),
         "dawn_set_option": ([vp, c_int, i64], c_int),
+        "dawn_get_trace": ([vp, vp, i32], c_int),
         "dawn_graph_info": ([vp, ctypes.POINTER(i32), ctypes.POINTER(i64), ctypes.POINTER(c_int)], c_int),
         "dawn_status_string": ([c_int], ctypes.c_char_p),
         "dawn_destroy": ([vp], None),
@@ -180,6 +182,21 @@ def dawn_get_stats(g: int) -> dict:
 
 def dawn_set_option(g: int, option: int, value: int):
     _check(load_library().dawn_set_option(ctypes.c_void_p(g), int(option), int(value)), "dawn_set_option")
+
+
+def dawn_get_trace(g: int, cap: int = 4096):
+    """Per-step rows of the last solve: list of (t_ns, frontier, edges) per
+    step, derived from the cumulative device trace."""
+    import numpy as np
+    buf = np.zeros(4 * cap, dtype=np.int64)
+    rows = load_library().dawn_get_trace(ctypes.c_void_p(g), ctypes.c_void_p(buf.ctypes.data), int(cap))
+    if rows < 0:
+        raise DawnError(-rows, "dawn_get_trace")
+    t = buf.reshape(-1, 4)[:rows]
+    out = []
+    for i in range(rows - 1):
+        out.append((int(t[i + 1, 0] - t[i, 0]), int(t[i + 1, 1] - t[i, 1]), int(t[i + 1, 2] - t[i, 2])))
+    return out
 
 
 def dawn_graph_info(g: int) -> tuple[int, int, int]:
