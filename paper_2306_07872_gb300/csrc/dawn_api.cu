@@ -29,9 +29,9 @@ struct dawn_graph_s {
   // solver workspace for up to ws_k instances
   int32_t ws_k = 0;
   unsigned long long *state = nullptr;
-  uint32_t *bm0 = nullptr, *bm1 = nullptr;
-  int2 *q0 = nullptr, *q1 = nullptr;
-  int32_t *t0 = nullptr, *t1 = nullptr;
+  uint32_t *bitmap = nullptr;
+  uint4 *queue = nullptr;
+  int32_t *tiles = nullptr;
   unsigned long long *tails = nullptr;
   int64_t words = 0, tiles_cap = 0;
   DeviceCtl *ctl = nullptr;
@@ -162,17 +162,14 @@ int dalloc(T **p, size_t count) {
 
 void free_workspace(dawn_graph g) {
   cudaFree(g->state);
-  cudaFree(g->bm0);
-  cudaFree(g->bm1);
-  cudaFree(g->q0);
-  cudaFree(g->q1);
-  cudaFree(g->t0);
-  cudaFree(g->t1);
+  cudaFree(g->bitmap);
+  cudaFree(g->queue);
+  cudaFree(g->tiles);
   cudaFree(g->tails);
   g->state = nullptr;
-  g->bm0 = g->bm1 = nullptr;
-  g->q0 = g->q1 = nullptr;
-  g->t0 = g->t1 = nullptr;
+  g->bitmap = nullptr;
+  g->queue = nullptr;
+  g->tiles = nullptr;
   g->tails = nullptr;
   g->ws_k = 0;
 }
@@ -182,7 +179,7 @@ void free_workspace(dawn_graph g) {
 int32_t max_chunk(dawn_graph g) {
   const int64_t tiles_cap = g->m / dawn::kTile + 2;
   int64_t by_tiles = (int64_t)0x7FFFFFFF / tiles_cap;
-  const int64_t per_inst = (int64_t)g->n * (8 + 16) + 2 * 4 * ((g->n + 31) / 32) + 2 * 4 * tiles_cap + 24;
+  const int64_t per_inst = (int64_t)g->n * (8 + 16) + 4 * ((g->n + 31) / 32) + 4 * tiles_cap + 16;
   size_t free_b = 0, total_b = 0;
   int64_t budget = (int64_t)48 << 30;
   if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) budget = std::min<int64_t>(budget, (int64_t)(free_b / 2));
@@ -197,10 +194,9 @@ int ensure_workspace(dawn_graph g, int32_t k) {
   g->tiles_cap = g->m / dawn::kTile + 2;
   const size_t kn = (size_t)k * g->n;
   int rc;
-  if ((rc = dalloc(&g->state, kn)) || (rc = dalloc(&g->bm0, (size_t)k * g->words)) ||
-      (rc = dalloc(&g->bm1, (size_t)k * g->words)) || (rc = dalloc(&g->q0, kn)) || (rc = dalloc(&g->q1, kn)) ||
-      (rc = dalloc(&g->t0, (size_t)k * g->tiles_cap)) || (rc = dalloc(&g->t1, (size_t)k * g->tiles_cap)) ||
-      (rc = dalloc(&g->tails, (size_t)3 * k))) {
+  if ((rc = dalloc(&g->state, kn)) || (rc = dalloc(&g->bitmap, (size_t)k * g->words)) ||
+      (rc = dalloc(&g->queue, kn)) || (rc = dalloc(&g->tiles, (size_t)k * g->tiles_cap)) ||
+      (rc = dalloc(&g->tails, (size_t)2 * k))) {
     free_workspace(g);
     return rc;
   }
@@ -235,12 +231,9 @@ int run_solve(dawn_graph g, const int32_t *seeds, int32_t nseeds, int32_t source
   p.nseeds = nseeds;
   p.source = source;
   p.state = g->state;
-  p.bitmap0 = g->bm0;
-  p.bitmap1 = g->bm1;
-  p.queue0 = g->q0;
-  p.queue1 = g->q1;
-  p.tiles0 = g->t0;
-  p.tiles1 = g->t1;
+  p.bitmap = g->bitmap;
+  p.queue = g->queue;
+  p.tiles = g->tiles;
   p.tails = g->tails;
   p.words = g->words;
   p.tiles_cap = g->tiles_cap;

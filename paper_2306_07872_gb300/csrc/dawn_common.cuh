@@ -1,22 +1,27 @@
 // Internal declarations shared by the CUDA translation units of libdawn.
 //
-// Data layout in device memory (one solver workspace per graph handle):
-//   state   u64 [k][n]   packed (key(dist) << 32) | parent edge.  key(d) is
-//                        d itself for uint32 weights and the IEEE bit pattern
-//                        for non-negative float32 weights; both are monotone
-//                        in d, so one 64-bit atomicMin updates the distance
-//                        and the parent edge together and keeps the
+// Data layout in device memory (one solver workspace per graph handle, k
+// instances):
+//   state   u64 [k][n]   alpha, packed (key(dist) << 32) | parent edge.
+//                        key(d) is d itself for uint32 weights and the IEEE
+//                        bit pattern for non-negative float32 weights; both
+//                        are monotone in d, so one 64-bit atomicMin updates
+//                        distance and parent edge together and keeps the
 //                        lexicographically smallest (dist, edge) pair.
-//   bitmap  u32 [2][k][words]   frontier membership (delta / beta of
-//                        Algorithm 2), one bit per vertex, double-buffered.
-//   queue   int2[2][k][n]  compacted frontier entries (vertex, offset of its
-//                        first out-edge in the frontier's virtual edge list).
-//   tiles   i32 [2][k][tiles_cap]  entry index that owns the first virtual
-//                        edge of every TILE-edge tile of the frontier.
-//   cw      uint2[m]     the CSR column and weight of every edge, interleaved.
-//   tails   u64 [3][k]   per-instance frontier size (low 32 bits) and total
-//                        out-degree (high 32 bits), updated by one atomicAdd
-//                        per warp so that entry order equals offset order.
+//   bitmap  u32 [k][words]   beta of Algorithm 2: vertices whose distance
+//                        dropped in the current step (one bit per vertex).
+//   queue   uint4[k][n]  delta of Algorithm 2, compacted: one entry per
+//                        frontier vertex with an out-edge = (row start,
+//                        offset of its first edge in the frontier's virtual
+//                        edge list, distance key, vertex id).
+//   tiles   i32 [k][tiles_cap]  entry index owning the first virtual edge of
+//                        every kTile-edge tile of the frontier.
+//   tails   u64 [2][k]   per-instance frontier size (low 32 bits) and total
+//                        out-degree (high 32 bits); one packed atomicAdd
+//                        reserves entries and edge offsets together, so the
+//                        queue order equals the offset order.
+//   cw      uint2[m]     (column, weight bits) of every CSR edge, interleaved
+//                        so that each edge is one 8-byte load.
 #pragma once
 
 #include <cstdint>
@@ -48,20 +53,20 @@ struct DeviceCtl {
 
 struct GovmParams {
   const int32_t *row_ptr;
-  const uint2 *cw;          // per edge: (column, weight bits), interleaved for one 8-byte load
-  const int32_t *src;       // tail of every edge
+  const uint2 *cw;           // per edge: (column, weight bits)
+  const int32_t *src;        // tail of every edge
   int32_t n;
   int64_t m;
-  int32_t k;                // instances in this launch
-  int32_t roots_mode;       // 0: seeds[i] is the source of instance i; 1: all seeds root instance 0
+  int32_t k;                 // instances in this launch
+  int32_t roots_mode;        // 0: seeds[i] is the source of instance i; 1: all seeds root instance 0
   const int32_t *seeds;      // device seeds, or null: then `source` is the only seed
   int32_t nseeds;
   int32_t source;
   unsigned long long *state;
-  uint32_t *bitmap0, *bitmap1;
-  int2 *queue0, *queue1;
-  int32_t *tiles0, *tiles1;
-  unsigned long long *tails;  // [3][k]
+  uint32_t *bitmap;
+  uint4 *queue;
+  int32_t *tiles;
+  unsigned long long *tails;  // [2][k]
   int64_t words;             // bitmap words per instance
   int64_t tiles_cap;         // tile slots per instance
   void *dist;                // [k][n] u32 or f32 bits

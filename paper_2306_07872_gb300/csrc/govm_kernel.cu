@@ -2,17 +2,23 @@
 // Algorithm 2) for sm_103a.
 //
 // One cooperative launch runs a whole solve:
-//   1. fill alpha with +inf (packed state), clear both frontier bitmaps;
-//   2. seed the frontier (the source of every instance, or all roots);
-//   3. GOVM steps until the frontier is empty:
-//        every warp takes 256-edge tiles of the frontier's virtual edge list
-//        (the concatenated out-edges of all frontier vertices, balanced by
-//        edges rather than vertices), relaxes each edge with a 64-bit packed
-//        atomicMin (distance and parent edge together), marks strictly
-//        improved vertices in the next bitmap (beta) and appends first-time
-//        marks to the next queue with one warp-aggregated atomicAdd that
-//        yields both the entry index and the entry's edge offset;
-//        a device-wide barrier (bounded wait) ends the step;
+//   1. alpha = +inf (packed state), beta = {} (bitmap);
+//   2. seeds: alpha[s] = 0 and s enters beta (every instance's source, or
+//      all roots);
+//   3. build delta from beta (below), then repeat GOVM steps:
+//      relax   every warp takes 256-edge tiles of the frontier's virtual edge
+//              list (the concatenated out-edges of all frontier vertices, so
+//              work is balanced by edges, not vertices), relaxes each edge
+//              with one 64-bit packed atomicMin (distance and parent edge
+//              together) and marks beta for every candidate that beats the
+//              distance it read; nothing on this path waits for an atomic's
+//              result except the update counter at the end of the tile;
+//      build   beta is consumed word by word and compacted into delta (one
+//              entry per marked vertex with an out-edge, ordered by vertex
+//              id), one block-aggregated atomicAdd per 256 words reserving
+//              entries and edge offsets together;
+//      each phase ends with a device-wide barrier (bounded wait); the loop
+//      stops when delta is empty (no path changed) or at the step cap;
 //   4. unpack dist / parent / parent_edge.
 // No host round trip happens between steps.
 #include <cuda_runtime.h>
@@ -65,23 +71,22 @@ struct Key<true> {
   }
 };
 
-constexpr int kStage = 2 * kTile;  // staged entries per warp (flushed above kStage - kTile)
-
 struct WarpTile {
-  int32_t rs[kTile + 1];     // CSR row start of each entry of the tile
+  uint32_t rs[kTile + 1];    // CSR row start of each entry overlapping the tile
   uint32_t off[kTile + 1];   // virtual offset of each entry's first edge
-  uint32_t dkey[kTile + 1];  // distance key of each entry's vertex (read at expansion time)
+  uint32_t dkey[kTile + 1];  // distance key of each entry's vertex
   int32_t own[kTile];        // owning entry (relative index) of every virtual edge
-  int32_t bv[kStage];        // staged next-frontier vertices
-  uint32_t bd[kStage];       // and their out-degrees
 };
 
 struct BlockShared {
   int32_t tprefix[kMaxInstancesPerLaunch + 1];
-  int32_t warp_sums[kWarpsPerBlock];
+  unsigned long long scan[kWarpsPerBlock];
+  unsigned long long base;
   int32_t flag;
   WarpTile wt[kWarpsPerBlock];
 };
+
+__device__ __forceinline__ void set_status(DeviceCtl *ctl, int code) { atomicCAS(&ctl->status, 0, code); }
 
 // Device-wide barrier with a bounded wait.  Returns false (uniformly for the
 // block) when the status word reports an error or the wait ran out.
@@ -101,7 +106,7 @@ __device__ bool grid_barrier(DeviceCtl *ctl, unsigned long long limit_ns, int32_
       while (ld_acquire_u32(&ctl->bar_gen) == gen) {
         if (ld_volatile_i32(&ctl->status) != 0) break;
         if (global_ns() - t0 > limit_ns) {
-          atomicCAS(&ctl->status, 0, (int)DAWN_ERR_TIMEOUT);
+          set_status(ctl, DAWN_ERR_TIMEOUT);
           break;
         }
         __nanosleep(ns);
@@ -115,192 +120,187 @@ __device__ bool grid_barrier(DeviceCtl *ctl, unsigned long long limit_ns, int32_
   return *s_flag != 0;
 }
 
-__device__ __forceinline__ void set_status(DeviceCtl *ctl, int code) { atomicCAS(&ctl->status, 0, code); }
+// Block-wide exclusive scan of one 64-bit value per thread; `total` receives
+// the block sum.  Must be reached by every thread of the block.
+__device__ __forceinline__ unsigned long long block_excl_scan(unsigned long long x, unsigned long long &total,
+                                                              BlockShared &sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  unsigned long long incl = x;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    unsigned long long o = __shfl_up_sync(kFull, incl, d);
+    if (lane >= d) incl += o;
+  }
+  if (lane == 31) sh.scan[warp] = incl;
+  __syncthreads();
+  unsigned long long before = 0, all = 0;
+#pragma unroll
+  for (int w = 0; w < kWarpsPerBlock; ++w) {
+    const unsigned long long s = sh.scan[w];
+    if (w < warp) before += s;
+    all += s;
+  }
+  __syncthreads();
+  total = all;
+  return before + incl - x;
+}
 
 // Exclusive prefix over instances of the number of tiles of each current
 // frontier (tiles = ceil(edges / kTile)).  Returns the total.
 __device__ int32_t scan_tiles(const unsigned long long *tails_cur, int32_t k, BlockShared &sh) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x;
   constexpr int kPer = kMaxInstancesPerLaunch / kBlockThreads;
   int32_t vals[kPer];
   int32_t sum = 0;
 #pragma unroll
   for (int q = 0; q < kPer; ++q) {
-    int i = tid * kPer + q;
+    const int i = tid * kPer + q;
     int32_t t = 0;
     if (i < k) {
-      uint32_t e = (uint32_t)(__ldcg(tails_cur + i) >> 32);
+      const uint32_t e = (uint32_t)(__ldcg(tails_cur + i) >> 32);
       t = (int32_t)((e + kTile - 1) / kTile);
     }
     vals[q] = t;
     sum += t;
   }
-  int32_t incl = sum;
-#pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    int32_t o = __shfl_up_sync(kFull, incl, d);
-    if (lane >= d) incl += o;
-  }
-  if (lane == 31) sh.warp_sums[warp] = incl;
-  __syncthreads();
-  if (warp == 0) {
-    int32_t x = lane < kWarpsPerBlock ? sh.warp_sums[lane] : 0;
-    int32_t xi = x;
-#pragma unroll
-    for (int d = 1; d < kWarpsPerBlock; d <<= 1) {
-      int32_t o = __shfl_up_sync(kFull, xi, d);
-      if (lane >= d) xi += o;
-    }
-    if (lane < kWarpsPerBlock) sh.warp_sums[lane] = xi - x;  // exclusive
-    if (lane == kWarpsPerBlock - 1) sh.tprefix[k] = xi;      // total (k <= kMaxInstancesPerLaunch)
-  }
-  __syncthreads();
-  int32_t base = sh.warp_sums[warp] + incl - sum;
+  unsigned long long total = 0;
+  int32_t base = (int32_t)block_excl_scan((unsigned long long)sum, total, sh);
 #pragma unroll
   for (int q = 0; q < kPer; ++q) {
-    int i = tid * kPer + q;
+    const int i = tid * kPer + q;
     if (i < k) sh.tprefix[i] = base;
     base += vals[q];
   }
+  if (tid == 0) sh.tprefix[k] = (int32_t)total;
   __syncthreads();
   return sh.tprefix[k];
 }
 
-// Largest i with tprefix[i] <= g.
+// Largest i with tprefix[i] <= g (skips instances with no tiles).
 __device__ __forceinline__ int32_t find_instance(const int32_t *tprefix, int32_t k, int32_t g) {
   int32_t lo = 0, hi = k;
   while (hi - lo > 1) {
-    int32_t mid = (lo + hi) >> 1;
+    const int32_t mid = (lo + hi) >> 1;
     if (tprefix[mid] <= g) lo = mid; else hi = mid;
   }
   return lo;
 }
 
-// Next-frontier entries found by a warp are staged in its shared-memory
-// buffer (vertex, out-degree) and appended to the instance's queue in bulk:
-// one atomicAdd on the packed tail (count | degree-sum << 32) per flush
-// reserves a block of entries and the matching block of virtual edges, so the
-// queue order equals the offset order.  Staging across tiles keeps the number
-// of atomics on the (single, hot) tail word low.
-
-// Stage the lanes' pending entries (bit r of mask: vertex tgt[r], out-degree
-// dg[r]); `count` is the warp-uniform number of staged entries.
-__device__ __forceinline__ void stage_entries(WarpTile &wt, int &count, unsigned mask,
-                                              const int32_t (&tgt)[kEdgesPerLane],
-                                              const uint32_t (&dg)[kEdgesPerLane]) {
-  const int lane = threadIdx.x & 31;
-  const int mine = __popc(mask);
-  int incl = mine;
-#pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    int o = __shfl_up_sync(kFull, incl, d);
-    if (lane >= d) incl += o;
-  }
-  int pos = count + incl - mine;
-#pragma unroll
-  for (int r = 0; r < kEdgesPerLane; ++r) {
-    if (mask & (1u << r)) {
-      wt.bv[pos] = tgt[r];
-      wt.bd[pos] = dg[r];
-      ++pos;
+// Build delta (queue + tile table + tails_next) from beta (the bitmap) for
+// every instance; consumes (clears) the bitmap.  The distance key stored in
+// an entry is read here: no relaxation runs between this phase and the next
+// relax phase, so it is as fresh as a read at expansion time.
+__device__ void build_frontier(const GovmParams &p, unsigned long long *tails_next, BlockShared &sh) {
+  const int tid = threadIdx.x;
+  const int64_t cpi = (p.words + kBlockThreads - 1) / kBlockThreads;  // 256-word chunks per instance
+  const int64_t chunks = cpi * p.k;
+  for (int64_t ch = blockIdx.x; ch < chunks; ch += gridDim.x) {
+    const int32_t inst = (int32_t)(ch / cpi);
+    const int64_t word = (ch - (int64_t)inst * cpi) * kBlockThreads + tid;
+    uint32_t *bm = p.bitmap + (size_t)inst * p.words;
+    uint32_t bits = 0;
+    if (word < p.words) {
+      bits = __ldcg(bm + word);
+      if (bits) bm[word] = 0u;
+    }
+    uint32_t cnt = 0, degsum = 0;
+    for (uint32_t b = bits; b; b &= b - 1) {
+      const int32_t v = (int32_t)(word * 32 + __ffs(b) - 1);
+      const uint32_t d = (uint32_t)(__ldg(p.row_ptr + v + 1) - __ldg(p.row_ptr + v));
+      cnt += d > 0;
+      degsum += d;
+    }
+    unsigned long long total = 0;
+    const unsigned long long excl = block_excl_scan(((unsigned long long)degsum << 32) | cnt, total, sh);
+    if (total == 0) continue;  // block-uniform
+    if (tid == 0) sh.base = atomicAdd(tails_next + inst, total);
+    __syncthreads();
+    const unsigned long long pos = sh.base + excl;
+    __syncthreads();  // sh.base is rewritten by the next chunk
+    if (cnt == 0) continue;
+    uint32_t idx = (uint32_t)pos;
+    uint32_t off = (uint32_t)(pos >> 32);
+    uint4 *q = p.queue + (size_t)inst * p.n;
+    int32_t *tl = p.tiles + (size_t)inst * p.tiles_cap;
+    const unsigned long long *st = p.state + (size_t)inst * p.n;
+    for (uint32_t b = bits; b; b &= b - 1) {
+      const int32_t v = (int32_t)(word * 32 + __ffs(b) - 1);
+      const uint32_t rs = (uint32_t)__ldg(p.row_ptr + v);
+      const uint32_t d = (uint32_t)__ldg(p.row_ptr + v + 1) - rs;
+      if (d == 0) continue;
+      if (idx >= (uint32_t)p.n) {  // cannot happen: each vertex has one bit
+        set_status(p.ctl, DAWN_ERR_BOUNDS);
+        break;
+      }
+      const uint32_t key = (uint32_t)(ld_relaxed_u64(st + v) >> 32);
+      q[idx] = make_uint4(rs, off, key, (uint32_t)v);
+      const uint32_t end = off + d;
+      for (uint32_t tb = (off + kTile - 1) / kTile; tb * (uint32_t)kTile < end; ++tb) {
+        if (tb >= (uint32_t)p.tiles_cap) {
+          set_status(p.ctl, DAWN_ERR_BOUNDS);
+          break;
+        }
+        tl[tb] = (int32_t)idx;
+      }
+      ++idx;
+      off = end;
     }
   }
-  count += __shfl_sync(kFull, incl, 31);
-  __syncwarp();
 }
 
-// Append the staged entries to instance inst's queue `nxt` and record, in the
-// next frontier's tile table, which entry owns the first edge of each tile.
-__device__ void flush_entries(const GovmParams &p, WarpTile &wt, int &count, int32_t inst, int nxt,
-                              unsigned long long *tails_next) {
-  const int lane = threadIdx.x & 31;
-  if (count == 0) return;
-  unsigned long long degsum = 0;
-  for (int i = lane; i < count; i += 32) degsum += wt.bd[i];
+// Results of a tile's atomicMins, inspected only when the warp's next tile
+// has issued its first loads, so the atomics' latency is not waited for on
+// its own.
+struct Pending {
+  unsigned need = 0;
+  uint32_t ckey[kEdgesPerLane];
+  uint32_t okey[kEdgesPerLane];
+};
+
+__device__ __forceinline__ void count_updates(Pending &pd, unsigned long long &updates) {
 #pragma unroll
-  for (int d = 16; d > 0; d >>= 1) degsum += __shfl_xor_sync(kFull, degsum, d);
-  unsigned long long base = 0;
-  if (lane == 0) base = atomicAdd(tails_next + inst, (degsum << 32) | (unsigned long long)count);
-  base = __shfl_sync(kFull, base, 0);
-  const uint32_t idx0 = (uint32_t)base;
-  uint32_t run = (uint32_t)(base >> 32);
-  int2 *q = (nxt ? p.queue1 : p.queue0) + (size_t)inst * p.n;
-  int32_t *tl = (nxt ? p.tiles1 : p.tiles0) + (size_t)inst * p.tiles_cap;
-  for (int b = 0; b < count; b += 32) {
-    const int i = b + lane;
-    const uint32_t d = i < count ? wt.bd[i] : 0u;
-    uint32_t incl = d;
-#pragma unroll
-    for (int s = 1; s < 32; s <<= 1) {
-      uint32_t o = __shfl_up_sync(kFull, incl, s);
-      if (lane >= s) incl += o;
-    }
-    if (i < count) {
-      const uint32_t idx = idx0 + (uint32_t)i;
-      const uint32_t off = run + incl - d;
-      if (idx >= (uint32_t)p.n) {  // cannot happen: the bitmap admits a vertex once per step
-        set_status(p.ctl, DAWN_ERR_BOUNDS);
-      } else {
-        q[idx] = make_int2(wt.bv[i], (int32_t)off);
-        const uint32_t end = off + d;
-        for (uint32_t tb = (off + kTile - 1) / kTile; tb * (uint32_t)kTile < end; ++tb) {
-          if (tb >= (uint32_t)p.tiles_cap) {
-            set_status(p.ctl, DAWN_ERR_BOUNDS);
-            break;
-          }
-          tl[tb] = (int32_t)idx;
-        }
-      }
-    }
-    run += __shfl_sync(kFull, incl, 31);
-  }
-  count = 0;
-  __syncwarp();
+  for (int r = 0; r < kEdgesPerLane; ++r)
+    if ((pd.need & (1u << r)) && pd.okey[r] > pd.ckey[r]) ++updates;
+  pd.need = 0;
 }
 
 // Relax the out-edges in virtual-edge tile t of instance inst's frontier.
 template <bool F32>
-__device__ __forceinline__ void process_tile(const GovmParams &p, WarpTile &wt, int32_t inst, int32_t t,
-                                             unsigned long long tail_cur, int32_t tiles_i, int cur,
-                                             int &staged, unsigned long long &updates) {
+__device__ __forceinline__ void relax_tile(const GovmParams &p, WarpTile &wt, int32_t inst, int32_t t,
+                                           unsigned long long tail_cur, int32_t tiles_i, Pending &pd,
+                                           unsigned long long &updates) {
   const int lane = threadIdx.x & 31;
   const uint32_t E = (uint32_t)(tail_cur >> 32);
   const int32_t c = (int32_t)(uint32_t)tail_cur;
   const uint32_t x0 = (uint32_t)t * kTile;
   const uint32_t xend = min(x0 + (uint32_t)kTile, E);
-  const int32_t *tiles = (cur ? p.tiles1 : p.tiles0) + (size_t)inst * p.tiles_cap;
-  const int2 *q = (cur ? p.queue1 : p.queue0) + (size_t)inst * p.n;
-  uint32_t *bm_cur = (cur ? p.bitmap1 : p.bitmap0) + (size_t)inst * p.words;
-  uint32_t *bm_next = (cur ? p.bitmap0 : p.bitmap1) + (size_t)inst * p.words;
+  const int32_t *tiles = p.tiles + (size_t)inst * p.tiles_cap;
+  const uint4 *q = p.queue + (size_t)inst * p.n;
+  uint32_t *bm = p.bitmap + (size_t)inst * p.words;
   unsigned long long *st = p.state + (size_t)inst * p.n;
   const unsigned long long kSourceState = (unsigned long long)kNoEdge;  // key 0, no parent edge
 
   __syncwarp();  // the previous tile of this warp has finished with wt
   const int32_t ia = __ldcg(tiles + t);
   const int32_t ib = (t + 1 < tiles_i) ? __ldcg(tiles + t + 1) : c - 1;
+  count_updates(pd, updates);
   const int32_t nent = ib - ia + 1;
   // a tile overlaps at most kTile + 1 entries (every entry has an out-edge)
   if (ia < 0 || ib >= c || nent < 1 || nent > kTile + 1) {
     if (lane == 0) set_status(p.ctl, DAWN_ERR_BOUNDS);
     return;
   }
-
-  // Load the entries overlapping the tile; clear the current-bitmap words of
-  // entries that start here (every entry starts in exactly one tile, so the
-  // whole current bitmap is zero when the step ends).
   for (int s = lane; s < kTile; s += 32) wt.own[s] = 0;
   __syncwarp();
   for (int32_t j = lane; j < nent; j += 32) {
-    int2 en = __ldcg(q + ia + j);
-    uint32_t off = (uint32_t)en.y;
-    int32_t v = en.x;
-    wt.rs[j] = __ldg(p.row_ptr + v);
-    wt.off[j] = off;
-    wt.dkey[j] = (uint32_t)(ld_relaxed_u64(st + v) >> 32);
-    if (off >= x0 && off < x0 + (uint32_t)kTile) {
-      bm_cur[v >> 5] = 0u;
-      if (j > 0) wt.own[off - x0] = j;
-    }
+    const uint4 en = __ldcg(q + ia + j);
+    wt.rs[j] = en.x;
+    wt.off[j] = en.y;
+    // alpha[j] is read in place, as Algorithm 2 does: improvements made
+    // earlier in this step are used at once (never worse than the key stored
+    // when the frontier was built)
+    wt.dkey[j] = min(en.z, (uint32_t)(ld_relaxed_u64(st + en.w) >> 32));
+    if (j > 0 && en.y >= x0 && en.y < x0 + (uint32_t)kTile) wt.own[en.y - x0] = j;
   }
   __syncwarp();
   // Inclusive max-scan of entry starts: own[s] = entry owning edge x0 + s.
@@ -315,7 +315,7 @@ __device__ __forceinline__ void process_tile(const GovmParams &p, WarpTile &wt, 
     int32_t incl = run;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
-      int32_t o = __shfl_up_sync(kFull, incl, d);
+      const int32_t o = __shfl_up_sync(kFull, incl, d);
       if (lane >= d) incl = max(incl, o);
     }
     int32_t excl = __shfl_up_sync(kFull, incl, 1);
@@ -333,14 +333,13 @@ __device__ __forceinline__ void process_tile(const GovmParams &p, WarpTile &wt, 
   unsigned valid = 0;
 #pragma unroll
   for (int r = 0; r < kEdgesPerLane; ++r) {
-    const int slot = r * 32 + lane;
-    const uint32_t x = x0 + slot;
+    const uint32_t x = x0 + r * 32 + lane;
     tgt[r] = 0;
     ckey[r] = 0;
     eidx[r] = 0;
     if (x < xend) {
-      const int32_t j = wt.own[slot];
-      const uint32_t e = (uint32_t)wt.rs[j] + (x - wt.off[j]);
+      const int32_t j = wt.own[r * 32 + lane];
+      const uint32_t e = wt.rs[j] + (x - wt.off[j]);
       if (e >= (uint32_t)p.m) {
         set_status(p.ctl, DAWN_ERR_BOUNDS);
         continue;
@@ -356,47 +355,25 @@ __device__ __forceinline__ void process_tile(const GovmParams &p, WarpTile &wt, 
 #pragma unroll
   for (int r = 0; r < kEdgesPerLane; ++r)
     curst[r] = (valid & (1u << r)) ? ld_relaxed_u64(st + tgt[r]) : 0ull;
-  // Relax: packed atomicMin where the candidate beats the current state.
-  unsigned need = 0;
-  unsigned long long old[kEdgesPerLane];
-  int32_t rp0[kEdgesPerLane], rp1[kEdgesPerLane];
+  // Relax.  A candidate that beats the distance read marks beta (the thread
+  // whose atomicMin strictly lowers a distance always read a larger value, so
+  // every strict improvement is marked); equal-distance candidates with a
+  // lower edge index only update the parent.
 #pragma unroll
   for (int r = 0; r < kEdgesPerLane; ++r) {
     const unsigned long long cand = ((unsigned long long)ckey[r] << 32) | eidx[r];
-    old[r] = 0;
-    rp0[r] = rp1[r] = 0;
+    pd.ckey[r] = ckey[r];
+    pd.okey[r] = 0;
     if ((valid & (1u << r)) && cand < curst[r] && curst[r] != kSourceState) {
-      need |= 1u << r;
-      rp0[r] = __ldg(p.row_ptr + tgt[r]);
-      rp1[r] = __ldg(p.row_ptr + tgt[r] + 1);
-      old[r] = atomicMin(st + tgt[r], cand);
+      pd.need |= 1u << r;
+      if (ckey[r] < (uint32_t)(curst[r] >> 32)) atomicOr(bm + (tgt[r] >> 5), 1u << (tgt[r] & 31));
+      pd.okey[r] = (uint32_t)(atomicMin(st + tgt[r], cand) >> 32);
     }
   }
-  // Strict improvements enter beta (first setter appends to the next queue).
-  unsigned mark = 0;
-  uint32_t obits[kEdgesPerLane], dg[kEdgesPerLane];
-#pragma unroll
-  for (int r = 0; r < kEdgesPerLane; ++r) {
-    obits[r] = 0;
-    dg[r] = 0;
-    if ((need & (1u << r)) && (uint32_t)(old[r] >> 32) > ckey[r]) {
-      ++updates;
-      dg[r] = (uint32_t)(rp1[r] - rp0[r]);
-      if (dg[r] > 0) {
-        mark |= 1u << r;
-        obits[r] = atomicOr(bm_next + (tgt[r] >> 5), 1u << (tgt[r] & 31));
-      }
-    }
-  }
-  unsigned mask = 0;
-#pragma unroll
-  for (int r = 0; r < kEdgesPerLane; ++r)
-    if ((mark & (1u << r)) && !(obits[r] & (1u << (tgt[r] & 31)))) mask |= 1u << r;
-  stage_entries(wt, staged, mask, tgt, dg);
 }
 
 template <bool F32>
-__global__ void __launch_bounds__(kBlockThreads) govm_kernel(GovmParams p) {
+__global__ void __launch_bounds__(kBlockThreads, 3) govm_kernel(GovmParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   BlockShared &sh = *reinterpret_cast<BlockShared *>(smem_raw);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -412,7 +389,7 @@ __global__ void __launch_bounds__(kBlockThreads) govm_kernel(GovmParams p) {
   // Test hook: one thread waits on a flag that nothing sets; the bounded
   // wait runs out and every block leaves through the barrier's error path.
   if (p.test_stall && blockIdx.x == 0 && tid == 0) {
-    unsigned long long t0 = global_ns();
+    const unsigned long long t0 = global_ns();
     while (ld_volatile_i32(&ctl->stall_flag) == 0) {
       if (global_ns() - t0 > p.wait_limit_ns) {
         set_status(ctl, DAWN_ERR_TIMEOUT);
@@ -422,77 +399,34 @@ __global__ void __launch_bounds__(kBlockThreads) govm_kernel(GovmParams p) {
     }
   }
 
-  // 1. alpha = +inf, empty frontiers.
+  // 1. alpha = +inf, beta = {}.
   for (int32_t i = 0; i < p.k; ++i) {
     unsigned long long *st = p.state + (size_t)i * p.n;
     for (long long v = gtid; v < p.n; v += gsize) st[v] = kInfState;
   }
-  for (long long i = gtid; i < (long long)p.k * p.words; i += gsize) {
-    p.bitmap0[i] = 0u;
-    p.bitmap1[i] = 0u;
-  }
-  for (long long i = gtid; i < 3LL * p.k; i += gsize) p.tails[i] = 0ull;
+  for (long long i = gtid; i < (long long)p.k * p.words; i += gsize) p.bitmap[i] = 0u;
+  for (long long i = gtid; i < 2LL * p.k; i += gsize) p.tails[i] = 0ull;
   if (!grid_barrier(ctl, p.wait_limit_ns, &sh.flag)) goto finish;
 
-  // 2. Seeds: alpha[s] = 0, delta = {s}.
-  if (!p.roots_mode) {
-    for (long long i = gtid; i < p.k; i += gsize) {
-      const int32_t s = p.seeds ? p.seeds[i] : p.source;
-      if (s < 0 || s >= p.n) {
-        set_status(ctl, DAWN_ERR_INVALID);
-        continue;
-      }
-      p.state[(size_t)i * p.n + s] = kSourceState;
-      const uint32_t deg = (uint32_t)(__ldg(p.row_ptr + s + 1) - __ldg(p.row_ptr + s));
-      if (deg == 0) continue;
-      p.queue0[(size_t)i * p.n] = make_int2(s, 0);
-      p.bitmap0[(size_t)i * p.words + (s >> 5)] = 1u << (s & 31);
-      int32_t *tl = p.tiles0 + (size_t)i * p.tiles_cap;
-      for (uint32_t tb = 0; tb * (uint32_t)kTile < deg; ++tb) tl[tb] = 0;
-      p.tails[i] = ((unsigned long long)deg << 32) | 1ull;
+  // 2. Seeds: alpha[s] = 0, s enters beta.
+  for (long long i = gtid; i < (p.roots_mode ? (long long)p.nseeds : (long long)p.k); i += gsize) {
+    const int32_t s = p.seeds ? p.seeds[i] : p.source;
+    if (s < 0 || s >= p.n) {
+      set_status(ctl, DAWN_ERR_INVALID);
+      continue;
     }
-  } else {
-    for (long long i = gtid; i < p.nseeds; i += gsize) {
-      const int32_t s = p.seeds[i];
-      if (s < 0 || s >= p.n) set_status(ctl, DAWN_ERR_INVALID);
-      else p.state[s] = kSourceState;
-    }
-    if (!grid_barrier(ctl, p.wait_limit_ns, &sh.flag)) goto finish;
-    // warp-uniform loop: every lane of a warp takes part in the append
-    const long long gw = gtid >> 5, nw = gsize >> 5;
-    int staged = 0;
-    for (long long b = gw * 32; b < p.nseeds; b += nw * 32) {
-      const long long i = b + lane;
-      int32_t tg[kEdgesPerLane] = {0};
-      uint32_t dgs[kEdgesPerLane] = {0};
-      unsigned mask = 0;
-      if (i < p.nseeds) {
-        const int32_t s = p.seeds[i];
-        if (s >= 0 && s < p.n) {
-          const uint32_t deg = (uint32_t)(__ldg(p.row_ptr + s + 1) - __ldg(p.row_ptr + s));
-          if (deg > 0) {
-            const uint32_t bit = 1u << (s & 31);
-            if (!(atomicOr(p.bitmap0 + (s >> 5), bit) & bit)) {
-              mask = 1;
-              tg[0] = s;
-              dgs[0] = deg;
-            }
-          }
-        }
-      }
-      stage_entries(sh.wt[warp], staged, mask, tg, dgs);
-      if (staged > kStage - 32) flush_entries(p, sh.wt[warp], staged, 0, 0, p.tails);
-    }
-    flush_entries(p, sh.wt[warp], staged, 0, 0, p.tails);
+    const int32_t inst = p.roots_mode ? 0 : (int32_t)i;
+    p.state[(size_t)inst * p.n + s] = kSourceState;
+    atomicOr(p.bitmap + (size_t)inst * p.words + (s >> 5), 1u << (s & 31));
   }
+  if (!grid_barrier(ctl, p.wait_limit_ns, &sh.flag)) goto finish;
+  build_frontier(p, p.tails, sh);
   if (!grid_barrier(ctl, p.wait_limit_ns, &sh.flag)) goto finish;
 
   // 3. GOVM steps.
   for (;; ++step) {
-    const int cur = (int)(step & 1);
-    unsigned long long *tails_cur = p.tails + (size_t)(step % 3) * p.k;
-    unsigned long long *tails_next = p.tails + (size_t)((step + 1) % 3) * p.k;
-    unsigned long long *tails_old = p.tails + (size_t)((step + 2) % 3) * p.k;
+    unsigned long long *tails_cur = p.tails + (size_t)(step & 1) * p.k;
+    unsigned long long *tails_next = p.tails + (size_t)((step + 1) & 1) * p.k;
     const int32_t total_tiles = scan_tiles(tails_cur, p.k, sh);
     if (total_tiles == 0) {
       quiescent = true;
@@ -517,25 +451,24 @@ __global__ void __launch_bounds__(kBlockThreads) govm_kernel(GovmParams p) {
         const unsigned long long tl = __ldcg(tails_cur + i);
         fs += (uint32_t)tl;
         es += tl >> 32;
-        tails_old[i] = 0ull;  // read last in the previous step; appended to in the next one
+        tails_next[i] = 0ull;  // last read in the previous step; filled by this step's build
       }
       if (fs) atomicAdd(&ctl->frontier_sum, fs);
       if (es) atomicAdd(&ctl->edges_scanned, es);
     }
+    // relax
     const int32_t gw = blockIdx.x * kWarpsPerBlock + warp;
     const int32_t nw = gridDim.x * kWarpsPerBlock;
-    int staged = 0;
-    int32_t staged_inst = 0;
+    Pending pd;
     for (int32_t g = gw; g < total_tiles; g += nw) {
       const int32_t inst = find_instance(sh.tprefix, p.k, g);
-      const int32_t t = g - sh.tprefix[inst];
-      const int32_t tiles_i = sh.tprefix[inst + 1] - sh.tprefix[inst];
-      if (staged > 0 && inst != staged_inst) flush_entries(p, sh.wt[warp], staged, staged_inst, cur ^ 1, tails_next);
-      staged_inst = inst;
-      process_tile<F32>(p, sh.wt[warp], inst, t, __ldcg(tails_cur + inst), tiles_i, cur, staged, updates);
-      if (staged > kStage - kTile) flush_entries(p, sh.wt[warp], staged, inst, cur ^ 1, tails_next);
+      relax_tile<F32>(p, sh.wt[warp], inst, g - sh.tprefix[inst], __ldcg(tails_cur + inst),
+                      sh.tprefix[inst + 1] - sh.tprefix[inst], pd, updates);
     }
-    flush_entries(p, sh.wt[warp], staged, staged_inst, cur ^ 1, tails_next);
+    count_updates(pd, updates);
+    if (!grid_barrier(ctl, p.wait_limit_ns, &sh.flag)) break;
+    // build the next frontier
+    build_frontier(p, tails_next, sh);
     if (!grid_barrier(ctl, p.wait_limit_ns, &sh.flag)) break;
   }
 
@@ -578,8 +511,6 @@ finish:
   }
 }
 
-}  // namespace
-
 // Shared memory exceeds the 48 KB static limit: opt in once per kernel.
 cudaError_t prepare_kernels() {
   static bool done = false;
@@ -591,6 +522,8 @@ cudaError_t prepare_kernels() {
   done = e == cudaSuccess;
   return e;
 }
+
+}  // namespace
 
 cudaError_t launch_govm(const GovmParams &p, int is_f32, int grid_blocks, cudaStream_t stream) {
   cudaError_t e = prepare_kernels();
