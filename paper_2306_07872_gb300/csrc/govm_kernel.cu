@@ -326,49 +326,63 @@ __device__ __forceinline__ void relax_tile(const GovmParams &p, WarpTile &wt, in
   }
   __syncwarp();
 
-  // Edge phase: lane handles edges x0 + 32 r + lane, r = 0..7 (coalesced rounds).
-  int32_t tgt[kEdgesPerLane];
-  uint32_t ckey[kEdgesPerLane];
+  // Edge phase: lane handles edges x0 + 32 r + lane, r = 0..7 (coalesced
+  // rounds).  Every load of a phase is issued before any result is used, so
+  // the eight requests of a lane are in flight together.
   uint32_t eidx[kEdgesPerLane];
   unsigned valid = 0;
+  bool bad = false;
 #pragma unroll
   for (int r = 0; r < kEdgesPerLane; ++r) {
     const uint32_t x = x0 + r * 32 + lane;
-    tgt[r] = 0;
-    ckey[r] = 0;
     eidx[r] = 0;
     if (x < xend) {
       const int32_t j = wt.own[r * 32 + lane];
       const uint32_t e = wt.rs[j] + (x - wt.off[j]);
-      if (e >= (uint32_t)p.m) {
-        set_status(p.ctl, DAWN_ERR_BOUNDS);
-        continue;
+      if (e < (uint32_t)p.m) {
+        valid |= 1u << r;
+        eidx[r] = e;
+      } else {
+        bad = true;
       }
-      valid |= 1u << r;
-      eidx[r] = e;
-      const uint2 cw = __ldcs(p.cw + e);
-      tgt[r] = (int32_t)cw.x;
-      ckey[r] = Key<F32>::add(wt.dkey[j], cw.y);
     }
   }
+  uint2 cw[kEdgesPerLane];
+#pragma unroll
+  for (int r = 0; r < kEdgesPerLane; ++r)
+    cw[r] = (valid & (1u << r)) ? __ldcs(p.cw + eidx[r]) : make_uint2(0u, 0u);
+  if (bad) set_status(p.ctl, DAWN_ERR_BOUNDS);
   unsigned long long curst[kEdgesPerLane];
 #pragma unroll
   for (int r = 0; r < kEdgesPerLane; ++r)
-    curst[r] = (valid & (1u << r)) ? ld_relaxed_u64(st + tgt[r]) : 0ull;
+    curst[r] = (valid & (1u << r)) ? ld_relaxed_u64(st + cw[r].x) : 0ull;
   // Relax.  A candidate that beats the distance read marks beta (the thread
   // whose atomicMin strictly lowers a distance always read a larger value, so
   // every strict improvement is marked); equal-distance candidates with a
   // lower edge index only update the parent.
+  uint32_t ckey[kEdgesPerLane];
+  unsigned need = 0;
 #pragma unroll
   for (int r = 0; r < kEdgesPerLane; ++r) {
+    ckey[r] = Key<F32>::add(wt.dkey[wt.own[r * 32 + lane]], cw[r].y);
     const unsigned long long cand = ((unsigned long long)ckey[r] << 32) | eidx[r];
-    pd.ckey[r] = ckey[r];
-    pd.okey[r] = 0;
-    if ((valid & (1u << r)) && cand < curst[r] && curst[r] != kSourceState) {
-      pd.need |= 1u << r;
-      if (ckey[r] < (uint32_t)(curst[r] >> 32)) atomicOr(bm + (tgt[r] >> 5), 1u << (tgt[r] & 31));
-      pd.okey[r] = (uint32_t)(atomicMin(st + tgt[r], cand) >> 32);
+    if ((valid & (1u << r)) && cand < curst[r] && curst[r] != kSourceState) need |= 1u << r;
+  }
+  unsigned long long old[kEdgesPerLane];
+#pragma unroll
+  for (int r = 0; r < kEdgesPerLane; ++r) {
+    old[r] = ~0ull;
+    if (need & (1u << r)) {
+      const uint32_t t = cw[r].x;
+      if (ckey[r] < (uint32_t)(curst[r] >> 32)) atomicOr(bm + (t >> 5), 1u << (t & 31));
+      old[r] = atomicMin(st + t, ((unsigned long long)ckey[r] << 32) | eidx[r]);
     }
+  }
+  pd.need = need;
+#pragma unroll
+  for (int r = 0; r < kEdgesPerLane; ++r) {
+    pd.ckey[r] = ckey[r];
+    pd.okey[r] = (uint32_t)(old[r] >> 32);
   }
 }
 
