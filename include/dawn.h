@@ -64,7 +64,9 @@ typedef struct {
   int64_t steps;         /* GOVM steps executed (frontier non-empty) */
   int64_t frontier_sum;  /* sum over steps of |delta| (frontier vertices, out-degree >= 1) */
   int64_t edges_scanned; /* sum over steps of the frontier's out-edges (edges relaxed) */
-  int64_t updates;       /* strict distance decreases (path updates, the paper's mu numerator) */
+  int64_t updates;       /* path updates: vertices whose distance strictly dropped in a step
+                            (they enter beta), counted once per step, summed over steps;
+                            updates / (reached vertices - sources) is the paper's mu */
   int64_t instances;     /* instances solved by the last call */
 } dawn_stats;
 

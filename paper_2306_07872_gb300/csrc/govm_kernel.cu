@@ -11,8 +11,8 @@
 //              work is balanced by edges, not vertices), relaxes each edge
 //              with one 64-bit packed atomicMin (distance and parent edge
 //              together) and marks beta for every candidate that beats the
-//              distance it read; nothing on this path waits for an atomic's
-//              result except the update counter at the end of the tile;
+//              distance it read; both are fire-and-forget reductions, so no
+//              warp waits for an atomic's result;
 //      build   beta is consumed word by word and compacted into delta (one
 //              entry per marked vertex with an out-edge, ordered by vertex
 //              id), one block-aggregated atomicAdd per 256 words reserving
@@ -190,7 +190,8 @@ __device__ __forceinline__ int32_t find_instance(const int32_t *tprefix, int32_t
 // every instance; consumes (clears) the bitmap.  The distance key stored in
 // an entry is read here: no relaxation runs between this phase and the next
 // relax phase, so it is as fresh as a read at expansion time.
-__device__ void build_frontier(const GovmParams &p, unsigned long long *tails_next, BlockShared &sh) {
+__device__ void build_frontier(const GovmParams &p, unsigned long long *tails_next, BlockShared &sh,
+                               unsigned long long &marked) {
   const int tid = threadIdx.x;
   const int64_t cpi = (p.words + kBlockThreads - 1) / kBlockThreads;  // 256-word chunks per instance
   const int64_t chunks = cpi * p.k;
@@ -203,6 +204,7 @@ __device__ void build_frontier(const GovmParams &p, unsigned long long *tails_ne
       bits = __ldcg(bm + word);
       if (bits) bm[word] = 0u;
     }
+    marked += __popc(bits);
     uint32_t cnt = 0, degsum = 0;
     for (uint32_t b = bits; b; b &= b - 1) {
       const int32_t v = (int32_t)(word * 32 + __ffs(b) - 1);
@@ -248,27 +250,10 @@ __device__ void build_frontier(const GovmParams &p, unsigned long long *tails_ne
   }
 }
 
-// Results of a tile's atomicMins, inspected only when the warp's next tile
-// has issued its first loads, so the atomics' latency is not waited for on
-// its own.
-struct Pending {
-  unsigned need = 0;
-  uint32_t ckey[kEdgesPerLane];
-  uint32_t okey[kEdgesPerLane];
-};
-
-__device__ __forceinline__ void count_updates(Pending &pd, unsigned long long &updates) {
-#pragma unroll
-  for (int r = 0; r < kEdgesPerLane; ++r)
-    if ((pd.need & (1u << r)) && pd.okey[r] > pd.ckey[r]) ++updates;
-  pd.need = 0;
-}
-
 // Relax the out-edges in virtual-edge tile t of instance inst's frontier.
 template <bool F32>
 __device__ __forceinline__ void relax_tile(const GovmParams &p, WarpTile &wt, int32_t inst, int32_t t,
-                                           unsigned long long tail_cur, int32_t tiles_i, Pending &pd,
-                                           unsigned long long &updates) {
+                                           unsigned long long tail_cur, int32_t tiles_i) {
   const int lane = threadIdx.x & 31;
   const uint32_t E = (uint32_t)(tail_cur >> 32);
   const int32_t c = (int32_t)(uint32_t)tail_cur;
@@ -283,7 +268,6 @@ __device__ __forceinline__ void relax_tile(const GovmParams &p, WarpTile &wt, in
   __syncwarp();  // the previous tile of this warp has finished with wt
   const int32_t ia = __ldcg(tiles + t);
   const int32_t ib = (t + 1 < tiles_i) ? __ldcg(tiles + t + 1) : c - 1;
-  count_updates(pd, updates);
   const int32_t nent = ib - ia + 1;
   // a tile overlaps at most kTile + 1 entries (every entry has an out-edge)
   if (ia < 0 || ib >= c || nent < 1 || nent > kTile + 1) {
@@ -368,21 +352,14 @@ __device__ __forceinline__ void relax_tile(const GovmParams &p, WarpTile &wt, in
     const unsigned long long cand = ((unsigned long long)ckey[r] << 32) | eidx[r];
     if ((valid & (1u << r)) && cand < curst[r] && curst[r] != kSourceState) need |= 1u << r;
   }
-  unsigned long long old[kEdgesPerLane];
+  // Both atomics are fire-and-forget reductions: nothing waits for them.
 #pragma unroll
   for (int r = 0; r < kEdgesPerLane; ++r) {
-    old[r] = ~0ull;
     if (need & (1u << r)) {
       const uint32_t t = cw[r].x;
       if (ckey[r] < (uint32_t)(curst[r] >> 32)) atomicOr(bm + (t >> 5), 1u << (t & 31));
-      old[r] = atomicMin(st + t, ((unsigned long long)ckey[r] << 32) | eidx[r]);
+      atomicMin(st + t, ((unsigned long long)ckey[r] << 32) | eidx[r]);
     }
-  }
-  pd.need = need;
-#pragma unroll
-  for (int r = 0; r < kEdgesPerLane; ++r) {
-    pd.ckey[r] = ckey[r];
-    pd.okey[r] = (uint32_t)(old[r] >> 32);
   }
 }
 
@@ -396,7 +373,8 @@ __global__ void __launch_bounds__(kBlockThreads, 3) govm_kernel(GovmParams p) {
   DeviceCtl *ctl = p.ctl;
   const unsigned long long kInfState = ((unsigned long long)Key<F32>::inf << 32) | kNoEdge;
   const unsigned long long kSourceState = (unsigned long long)kNoEdge;
-  unsigned long long updates = 0;
+  unsigned long long updates = 0;  // vertices entering beta, summed over steps
+  unsigned long long seeded = 0;   // the seeds' own marks (not path updates)
   long long step = 0;
   bool quiescent = false;
 
@@ -434,7 +412,7 @@ __global__ void __launch_bounds__(kBlockThreads, 3) govm_kernel(GovmParams p) {
     atomicOr(p.bitmap + (size_t)inst * p.words + (s >> 5), 1u << (s & 31));
   }
   if (!grid_barrier(ctl, p.wait_limit_ns, &sh.flag)) goto finish;
-  build_frontier(p, p.tails, sh);
+  build_frontier(p, p.tails, sh, seeded);
   if (!grid_barrier(ctl, p.wait_limit_ns, &sh.flag)) goto finish;
 
   // 3. GOVM steps.
@@ -473,16 +451,14 @@ __global__ void __launch_bounds__(kBlockThreads, 3) govm_kernel(GovmParams p) {
     // relax
     const int32_t gw = blockIdx.x * kWarpsPerBlock + warp;
     const int32_t nw = gridDim.x * kWarpsPerBlock;
-    Pending pd;
     for (int32_t g = gw; g < total_tiles; g += nw) {
       const int32_t inst = find_instance(sh.tprefix, p.k, g);
       relax_tile<F32>(p, sh.wt[warp], inst, g - sh.tprefix[inst], __ldcg(tails_cur + inst),
-                      sh.tprefix[inst + 1] - sh.tprefix[inst], pd, updates);
+                      sh.tprefix[inst + 1] - sh.tprefix[inst]);
     }
-    count_updates(pd, updates);
     if (!grid_barrier(ctl, p.wait_limit_ns, &sh.flag)) break;
     // build the next frontier
-    build_frontier(p, tails_next, sh);
+    build_frontier(p, tails_next, sh, updates);
     if (!grid_barrier(ctl, p.wait_limit_ns, &sh.flag)) break;
   }
 
