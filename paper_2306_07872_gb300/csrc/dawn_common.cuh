@@ -30,7 +30,7 @@
 
 namespace dawn {
 
-constexpr int kTile = 256;           // virtual edges per warp task
+constexpr int kTile = 128;           // virtual edges per warp task
 constexpr int kEdgesPerLane = kTile / 32;
 constexpr int kBlockThreads = 256;   // persistent kernel block size
 constexpr int kWarpsPerBlock = kBlockThreads / 32;

@@ -6,7 +6,7 @@
 //   2. seeds: alpha[s] = 0 and s enters beta (every instance's source, or
 //      all roots);
 //   3. build delta from beta (below), then repeat GOVM steps:
-//      relax   every warp takes 256-edge tiles of the frontier's virtual edge
+//      relax   every warp takes 128-edge tiles of the frontier's virtual edge
 //              list (the concatenated out-edges of all frontier vertices, so
 //              work is balanced by edges, not vertices), relaxes each edge
 //              with one 64-bit packed atomicMin (distance and parent edge
@@ -187,65 +187,91 @@ __device__ __forceinline__ int32_t find_instance(const int32_t *tprefix, int32_t
 }
 
 // Build delta (queue + tile table + tails_next) from beta (the bitmap) for
-// every instance; consumes (clears) the bitmap.  The distance key stored in
-// an entry is read here: no relaxation runs between this phase and the next
-// relax phase, so it is as fresh as a read at expansion time.
+// every instance; consumes (clears) the bitmap.  A block takes 256 bitmap
+// words; each warp takes 32 of them and walks them one word at a time with
+// lane l handling vertex 32 w + l, so the row_ptr and state reads of a word
+// are coalesced.  The distance key stored in an entry is read here: no
+// relaxation runs between this phase and the next relax phase.
 __device__ void build_frontier(const GovmParams &p, unsigned long long *tails_next, BlockShared &sh,
                                unsigned long long &marked) {
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t cpi = (p.words + kBlockThreads - 1) / kBlockThreads;  // 256-word chunks per instance
   const int64_t chunks = cpi * p.k;
   for (int64_t ch = blockIdx.x; ch < chunks; ch += gridDim.x) {
     const int32_t inst = (int32_t)(ch / cpi);
-    const int64_t word = (ch - (int64_t)inst * cpi) * kBlockThreads + tid;
+    const int64_t w0 = (ch - (int64_t)inst * cpi) * kBlockThreads + warp * 32;  // this warp's first word
     uint32_t *bm = p.bitmap + (size_t)inst * p.words;
-    uint32_t bits = 0;
-    if (word < p.words) {
-      bits = __ldcg(bm + word);
-      if (bits) bm[word] = 0u;
+    uint32_t mine = 0;  // word w0 + lane
+    if (w0 + lane < p.words) {
+      mine = __ldcg(bm + w0 + lane);
+      if (mine) bm[w0 + lane] = 0u;
     }
-    marked += __popc(bits);
+    marked += __popc(mine);
+    // pass 1: entries and edges of this warp's words
     uint32_t cnt = 0, degsum = 0;
-    for (uint32_t b = bits; b; b &= b - 1) {
-      const int32_t v = (int32_t)(word * 32 + __ffs(b) - 1);
-      const uint32_t d = (uint32_t)(__ldg(p.row_ptr + v + 1) - __ldg(p.row_ptr + v));
+    unsigned nz = __ballot_sync(kFull, mine != 0);
+    for (unsigned z = nz; z; z &= z - 1) {
+      const int i = __ffs(z) - 1;
+      const uint32_t bits = __shfl_sync(kFull, mine, i);
+      uint32_t d = 0;
+      if ((bits >> lane) & 1u) {
+        const int32_t v = (int32_t)((w0 + i) * 32 + lane);
+        d = (uint32_t)(__ldg(p.row_ptr + v + 1) - __ldg(p.row_ptr + v));
+      }
       cnt += d > 0;
       degsum += d;
     }
+    unsigned long long wsum = ((unsigned long long)degsum << 32) | cnt;
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) wsum += __shfl_xor_sync(kFull, wsum, d);
     unsigned long long total = 0;
-    const unsigned long long excl = block_excl_scan(((unsigned long long)degsum << 32) | cnt, total, sh);
+    const unsigned long long wexcl = block_excl_scan(lane == 0 ? wsum : 0ull, total, sh);
     if (total == 0) continue;  // block-uniform
     if (tid == 0) sh.base = atomicAdd(tails_next + inst, total);
     __syncthreads();
-    const unsigned long long pos = sh.base + excl;
+    unsigned long long pos = sh.base + __shfl_sync(kFull, wexcl, 0);
     __syncthreads();  // sh.base is rewritten by the next chunk
-    if (cnt == 0) continue;
-    uint32_t idx = (uint32_t)pos;
-    uint32_t off = (uint32_t)(pos >> 32);
+    // pass 2: write the entries in (word, lane) order
     uint4 *q = p.queue + (size_t)inst * p.n;
     int32_t *tl = p.tiles + (size_t)inst * p.tiles_cap;
     const unsigned long long *st = p.state + (size_t)inst * p.n;
-    for (uint32_t b = bits; b; b &= b - 1) {
-      const int32_t v = (int32_t)(word * 32 + __ffs(b) - 1);
-      const uint32_t rs = (uint32_t)__ldg(p.row_ptr + v);
-      const uint32_t d = (uint32_t)__ldg(p.row_ptr + v + 1) - rs;
-      if (d == 0) continue;
-      if (idx >= (uint32_t)p.n) {  // cannot happen: each vertex has one bit
-        set_status(p.ctl, DAWN_ERR_BOUNDS);
-        break;
+    for (unsigned z = nz; z; z &= z - 1) {
+      const int i = __ffs(z) - 1;
+      const uint32_t bits = __shfl_sync(kFull, mine, i);
+      const int32_t v = (int32_t)((w0 + i) * 32 + lane);
+      uint32_t rs = 0, d = 0, key = 0;
+      if ((bits >> lane) & 1u) {
+        rs = (uint32_t)__ldg(p.row_ptr + v);
+        d = (uint32_t)__ldg(p.row_ptr + v + 1) - rs;
+        if (d > 0) key = (uint32_t)(ld_relaxed_u64(st + v) >> 32);
       }
-      const uint32_t key = (uint32_t)(ld_relaxed_u64(st + v) >> 32);
-      q[idx] = make_uint4(rs, off, key, (uint32_t)v);
-      const uint32_t end = off + d;
-      for (uint32_t tb = (off + kTile - 1) / kTile; tb * (uint32_t)kTile < end; ++tb) {
-        if (tb >= (uint32_t)p.tiles_cap) {
+      // lane prefix of (entries, edges) within this word
+      unsigned long long x = ((unsigned long long)d << 32) | (d > 0 ? 1u : 0u);
+      unsigned long long incl = x;
+#pragma unroll
+      for (int s = 1; s < 32; s <<= 1) {
+        const unsigned long long o = __shfl_up_sync(kFull, incl, s);
+        if (lane >= s) incl += o;
+      }
+      if (d > 0) {
+        const unsigned long long at = pos + incl - x;
+        const uint32_t idx = (uint32_t)at;
+        const uint32_t off = (uint32_t)(at >> 32);
+        if (idx >= (uint32_t)p.n) {  // cannot happen: each vertex has one bit
           set_status(p.ctl, DAWN_ERR_BOUNDS);
-          break;
+        } else {
+          q[idx] = make_uint4(rs, off, key, (uint32_t)v);
+          const uint32_t end = off + d;
+          for (uint32_t tb = (off + kTile - 1) / kTile; tb * (uint32_t)kTile < end; ++tb) {
+            if (tb >= (uint32_t)p.tiles_cap) {
+              set_status(p.ctl, DAWN_ERR_BOUNDS);
+              break;
+            }
+            tl[tb] = (int32_t)idx;
+          }
         }
-        tl[tb] = (int32_t)idx;
       }
-      ++idx;
-      off = end;
+      pos += __shfl_sync(kFull, incl, 31);
     }
   }
 }
@@ -364,7 +390,7 @@ __device__ __forceinline__ void relax_tile(const GovmParams &p, WarpTile &wt, in
 }
 
 template <bool F32>
-__global__ void __launch_bounds__(kBlockThreads, 3) govm_kernel(GovmParams p) {
+__global__ void __launch_bounds__(kBlockThreads, 5) govm_kernel(GovmParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   BlockShared &sh = *reinterpret_cast<BlockShared *>(smem_raw);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
