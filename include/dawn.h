@@ -204,6 +204,34 @@ int dawn_get_trace(dawn_graph g, int64_t *out, int32_t cap);
 /* Basic graph facts: n, m and the weight type. */
 int dawn_graph_info(dawn_graph g, int32_t *n, int64_t *m, int *wtype);
 
+/*
+ * Allocation-free variant of dawn_sssp (the paper has no counterpart; this is
+ * a deployment convenience of the library).
+ *
+ * For callers that cannot allocate device memory during a call (a memory
+ * budget fixed up front, hosts that forbid allocator calls after start-up,
+ * or code that must avoid the implicit synchronisation of cudaMalloc /
+ * cudaFree), this entry point runs the same GOVM solve as dawn_sssp but takes
+ * its whole per-solve workspace from one fixed array of 32 MiB in device
+ * global memory that belongs to the library (every GPU that loads the
+ * library holds this array until the process exits).  It calls no
+ * allocation routine.
+ *   g            a graph created earlier with dawn_create_graph
+ *   source, dist, parent, parent_edge   as for dawn_sssp
+ *   status_out   device int32 or NULL: receives the solve's device-side
+ *                status (DAWN_OK or an error code) when the solve ends
+ * Limit: the workspace needs about 24 bytes per vertex plus 4 bytes per 128
+ * edges; a graph that does not fit in 32 MiB is rejected with
+ * DAWN_ERR_INVALID before anything is enqueued.
+ * The first call on a device looks up the array's device address (once per
+ * device); make that first call before any stream capture.  Every call uses
+ * the same array and leaves its contents behind (the call clears what must
+ * start at zero), so calls that overlap on the GPU, on any stream or handle,
+ * race and must not be issued.
+ */
+int dawn_sssp_noalloc(dawn_graph g, int32_t source, void *dist, int32_t *parent, int32_t *parent_edge,
+                      int32_t *status_out, void *stream);
+
 /* Human-readable name of a status code (static string). */
 const char *dawn_status_string(int code);
 

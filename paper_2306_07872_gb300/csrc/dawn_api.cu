@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cstdint>
 #include <cstring>
+#include <mutex>
 #include <new>
 
 #include "dawn_common.cuh"
@@ -523,3 +524,105 @@ void dawn_destroy(dawn_graph g) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free single-source solve.
+//
+// Some callers cannot allocate device memory while they run: code that
+// executes inside a memory budget fixed up front, real-time or embedded
+// hosts that forbid allocator calls after start-up, and callers that must not
+// trigger the implicit synchronisation of cudaMalloc / cudaFree.  For them,
+// dawn_sssp_noalloc runs the same GOVM kernel with its whole per-solve
+// workspace carved out of one fixed-size array in device global memory that
+// is part of this library (every GPU that loads the library holds it until
+// the process exits).
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = (size_t)32 << 20;  // 32 MiB
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+void *g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device.  In host code
+// the array's name only stands in for the symbol; the address comes from
+// cudaGetSymbolAddress, looked up once per device (on the first call).
+int noalloc_scratch(int device, unsigned char **out) {
+  if (device < 0 || device >= kMaxDevices) return DAWN_ERR_CUDA;
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[device]) {
+    void *ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) {
+      cudaGetLastError();
+      return DAWN_ERR_CUDA;
+    }
+    g_noalloc_ptr[device] = ptr;
+  }
+  *out = (unsigned char *)g_noalloc_ptr[device];
+  return DAWN_OK;
+}
+
+}  // namespace
+
+extern "C" int dawn_sssp_noalloc(dawn_graph g, int32_t source, void *dist, int32_t *parent, int32_t *parent_edge,
+                                 int32_t *status_out, void *stream) {
+  if (!g || !dist || source < 0 || source >= g->n) return DAWN_ERR_INVALID;
+  if (set_device(g)) return DAWN_ERR_CUDA;
+  // workspace layout inside the fixed array (each piece 256-byte aligned)
+  const int64_t words = (g->n + 31) / 32;
+  const int64_t tiles_cap = g->m / dawn::kTile + 2;
+  size_t used = 0;
+  auto take = [&used](size_t bytes) {
+    const size_t at = used;
+    used = (used + bytes + 255) & ~(size_t)255;
+    return at;
+  };
+  const size_t o_ctl = take(sizeof(DeviceCtl));
+  const size_t o_tails = take(2 * sizeof(unsigned long long));
+  const size_t o_state = take((size_t)g->n * sizeof(unsigned long long));
+  const size_t o_bitmap = take((size_t)words * sizeof(uint32_t));
+  const size_t o_queue = take((size_t)g->n * sizeof(uint4));
+  const size_t o_tiles = take((size_t)tiles_cap * sizeof(int32_t));
+  if (used > kNoAllocScratchBytes) return DAWN_ERR_INVALID;  // graph too large for the fixed scratch
+  unsigned char *base = nullptr;
+  int rc = noalloc_scratch(g->device, &base);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  DeviceCtl *ctl = (DeviceCtl *)(base + o_ctl);
+  GovmParams p = {};
+  p.row_ptr = g->row_ptr;
+  p.cw = g->cw;
+  p.src = g->src;
+  p.n = g->n;
+  p.m = g->m;
+  p.k = 1;
+  p.roots_mode = 0;
+  p.seeds = nullptr;
+  p.nseeds = 1;
+  p.source = source;
+  p.state = (unsigned long long *)(base + o_state);
+  p.bitmap = (uint32_t *)(base + o_bitmap);
+  p.queue = (uint4 *)(base + o_queue);
+  p.tiles = (int32_t *)(base + o_tiles);
+  p.tails = (unsigned long long *)(base + o_tails);
+  p.words = words;
+  p.tiles_cap = tiles_cap;
+  p.dist = dist;
+  p.parent = parent;
+  p.parent_edge = parent_edge;
+  p.ctl = ctl;
+  p.max_steps = g->max_steps > 0 ? g->max_steps : g->n;
+  p.wait_limit_ns = g->wait_limit_ns;
+  p.test_stall = 0;
+  p.trace = nullptr;
+  p.trace_cap = 0;
+  // the control block (barrier counters, status) must start at zero; the
+  // kernel itself resets everything else it reads
+  cudaError_t e = cudaMemsetAsync(ctl, 0, sizeof(DeviceCtl), s);
+  if (e == cudaSuccess) e = dawn::launch_govm(p, g->wtype == DAWN_W_F32, grid_for(g, 1), s);
+  if (e == cudaSuccess && status_out)
+    e = cudaMemcpyAsync(status_out, &ctl->status, sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
+  if (e != cudaSuccess) return cuda_fail(e);
+  return DAWN_OK;
+}

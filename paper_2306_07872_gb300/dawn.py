@@ -29,7 +29,7 @@ DAWN_OPT_TRACE_STEPS = 5
 
 EXPORTS = ("dawn_create_graph", "dawn_set_weights", "dawn_reserve", "dawn_sssp", "dawn_msssp", "dawn_sssp_roots",
            "dawn_sssp_backward", "dawn_status", "dawn_get_stats", "dawn_set_option", "dawn_get_trace", "dawn_graph_info",
-           "dawn_status_string", "dawn_destroy")
+           "dawn_status_string", "dawn_destroy", "dawn_sssp_noalloc")
 
 
 class DawnError(RuntimeError):
@@ -69,6 +69,7 @@ def load_library(path: str = LIB_PATH):
         "dawn_graph_info": ([vp, ctypes.POINTER(i32), ctypes.POINTER(i64), ctypes.POINTER(c_int)], c_int),
         "dawn_status_string": ([c_int], ctypes.c_char_p),
         "dawn_destroy": ([vp], None),
+        "dawn_sssp_noalloc": ([vp, i32, vp, vp, vp, vp, vp], c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -148,6 +149,17 @@ def dawn_sssp(g: int, source: int, dist: torch.Tensor, parent=None, parent_edge=
     _check(load_library().dawn_sssp(ctypes.c_void_p(g), int(source), _dev(dist, name="dist"),
                                     _dev(parent, torch.int32, "parent"), _dev(parent_edge, torch.int32, "parent_edge"),
                                     _stream(stream)), "dawn_sssp")
+
+
+def dawn_sssp_noalloc(g: int, source: int, dist: torch.Tensor, parent=None, parent_edge=None, status_out=None,
+                      stream=None):
+    """dawn_sssp without any allocation: the workspace comes from the
+    library's fixed 32 MiB device array (see include/dawn.h)."""
+    _check(load_library().dawn_sssp_noalloc(ctypes.c_void_p(g), int(source), _dev(dist, name="dist"),
+                                            _dev(parent, torch.int32, "parent"),
+                                            _dev(parent_edge, torch.int32, "parent_edge"),
+                                            _dev(status_out, torch.int32, "status_out"), _stream(stream)),
+           "dawn_sssp_noalloc")
 
 
 def dawn_msssp(g: int, sources: torch.Tensor, dist: torch.Tensor, parent=None, stream=None):
