@@ -108,16 +108,22 @@ class Clocks:
 
 # ------------------------------------------------------------------ workloads
 
+def shard(sources, per_rank: int, rank: int):
+    """This rank's sources: a disjoint block of `per_rank` of all ranks'
+    sources (weak scaling: per-GPU work is fixed as ranks are added)."""
+    return sources[rank * per_rank:(rank + 1) * per_rank]
+
+
 def make_workload(name: str, rank: int = 0, world: int = 1):
     import graphgen as gg
     if name.startswith("rmat") and name[4:].isdigit():
         # rmat22 is the benchmark workload; smaller scales serve profiling
         wl = gg.rmat_u32(int(name[4:]), 16, nsrc=64 * world, seed=0)
-        wl.sources = wl.sources[rank * 64:(rank + 1) * 64]
+        wl.sources = shard(wl.sources, 64, rank)
         return wl
     if name == "grid":
         wl = gg.grid_f32(2048, 0.01, nsrc=16 * world, seed=0)
-        wl.sources = wl.sources[rank * 16:(rank + 1) * 16]
+        wl.sources = shard(wl.sources, 16, rank)
         return wl
     if name == "tiny":
         return gg.tiny_er()
@@ -278,6 +284,120 @@ def cpu_baseline(wl, budget_s: float = 20.0):
             "mu_oracle": float(np.mean([r[1]["mu"] for r in res]))}
 
 
+# ------------------------------------------------- batched and differentiable
+
+def _time(fn, reps=3, warm=1):
+    import torch
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps / 1e3
+
+
+def run_batched(args):
+    """Pattern 2: (a) 1024 sources of an R-MAT s18 graph in batched launches
+    (dawn_msssp) vs a loop of single-source solves; (b) 64 uneven ER graphs
+    solved as one multi-root forest on their disjoint union
+    (dawn_sssp_roots) vs a loop of per-graph solves."""
+    import torch
+    import graphgen as gg
+    import paper_2306_07872_gb300 as dawn
+    out = {}
+    wl = gg.rmat_u32(18, 16, nsrc=1024, seed=0)
+    g = dawn.Graph(wl.row_ptr, wl.col, wl.weights)
+    src = torch.from_numpy(wl.sources).cuda()
+    k = len(wl.sources)
+    dist = torch.empty((k, wl.n), dtype=torch.uint32, device="cuda")
+    par = torch.empty((k, wl.n), dtype=torch.int32, device="cuda")
+    dawn.dawn_reserve(g.handle, k)
+    t_batch = _time(lambda: dawn.dawn_msssp(g.handle, src, dist, par))
+    g.check()
+    st = g.stats()
+    srcs = [int(x) for x in wl.sources]
+    def loop():
+        for i, s_ in enumerate(srcs):
+            dawn.dawn_sssp(g.handle, s_, dist[i], par[i], None)
+    t_loop = _time(loop)
+    g.check()
+    out["msssp_rmat18_1024"] = {"batched_s": t_batch, "loop_s": t_loop, "speedup": t_loop / t_batch,
+                                "gteps_batched": k * wl.e_wcc / t_batch / 1e9,
+                                "gteps_loop": k * wl.e_wcc / t_loop / 1e9,
+                                "edges_scanned_per_instance": st["edges_scanned"] / k,
+                                "updates_per_instance": st["updates"] / k}
+    del dist, par
+    g.close()
+    torch.cuda.empty_cache()
+    wb = gg.er_batch(count=64, seed=0)
+    gu = dawn.Graph(wb.row_ptr, wb.col, wb.weights)
+    roots = torch.from_numpy(wb.sources).cuda()
+    du = torch.empty(wb.n, dtype=torch.uint32, device="cuda")
+    pu = torch.empty(wb.n, dtype=torch.int32, device="cuda")
+    t_roots = _time(lambda: dawn.dawn_sssp_roots(gu.handle, roots, du, pu))
+    gu.check()
+    offs = wb.extra["offsets"]
+    parts = []
+    for i in range(64):
+        a, b = int(offs[i]), int(offs[i + 1])
+        e0, e1 = int(wb.row_ptr[a]), int(wb.row_ptr[b])
+        rp = (wb.row_ptr[a:b + 1] - e0).astype(np.int32)
+        parts.append(dawn.Graph(rp, (wb.col[e0:e1] - a).astype(np.int32), wb.weights[e0:e1]))
+    outs = [(torch.empty(p_.n, dtype=torch.uint32, device="cuda"), torch.empty(p_.n, dtype=torch.int32, device="cuda"))
+            for p_ in parts]
+    def loop2():
+        for p_, (d_, pp_) in zip(parts, outs):
+            dawn.dawn_sssp(p_.handle, 0, d_, pp_, None)
+    t_loop2 = _time(loop2)
+    for p_ in parts:
+        p_.check()
+    out["roots_er64"] = {"one_launch_s": t_roots, "loop_s": t_loop2, "speedup": t_loop2 / t_roots,
+                         "gteps_one_launch": wb.m / t_roots / 1e9, "gteps_loop": wb.m / t_loop2 / 1e9,
+                         "n": wb.n, "m": wb.m}
+    for p_ in parts:
+        p_.close()
+    gu.close()
+    return out
+
+
+def run_diff(args):
+    """Pattern 3 on R-MAT s16 fp32: plain solve, forward (weights loaded +
+    solve saving the parent tree) and forward + backward."""
+    import torch
+    import graphgen as gg
+    import paper_2306_07872_gb300 as dawn
+    wl = gg.rmat_f32_diff(scale=16, edge_factor=16, ntargets=256, seed=0)
+    g = dawn.Graph(wl.row_ptr, wl.col, wl.weights)
+    w = torch.from_numpy(wl.weights).cuda()
+    tg = torch.from_numpy(wl.extra["targets"]).long().cuda()
+    cf = torch.from_numpy(wl.extra["coef"]).float().cuda()
+    dist = torch.empty(wl.n, dtype=torch.float32, device="cuda")
+    pe = torch.empty(wl.n, dtype=torch.int32, device="cuda")
+    t_plain = _time(lambda: dawn.dawn_sssp(g.handle, 0, dist, None, pe), reps=20, warm=3)
+    def fwd():
+        return dawn.DawnSSSP.apply(w, g, 0)
+    t_fwd = _time(fwd, reps=20, warm=3)
+    def fwd_bwd():
+        ww = w.clone().requires_grad_(True)
+        d = dawn.DawnSSSP.apply(ww, g, 0)
+        (d[tg] * cf).sum().backward()
+    t_fb = _time(fwd_bwd, reps=20, warm=3)
+    grad_dist = torch.zeros(wl.n, dtype=torch.float32, device="cuda")
+    grad_dist[tg] = cf
+    grad_w = torch.empty(wl.m, dtype=torch.float32, device="cuda")
+    t_bwd = _time(lambda: dawn.dawn_sssp_backward(g.handle, pe, grad_dist, grad_w), reps=20, warm=3)
+    g.check()
+    g.close()
+    return {"diff_rmat16_f32": {"plain_sssp_s": t_plain, "forward_s": t_fwd, "forward_backward_s": t_fb,
+                                "backward_kernel_s": t_bwd, "fb_over_plain": t_fb / t_plain,
+                                "n": wl.n, "m": wl.m}}
+
+
 # ----------------------------------------------------------------- plumbing
 
 def barrier(world):
@@ -379,6 +499,11 @@ def main_ours(args):
             "e2e": e2e, "gpu_launches": res["launches"], "clocks": res["clocks"], "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
+    elif args.workload in ("batched", "diff"):
+        if world > 1 and rank != 0:
+            return
+        res = run_batched(args) if args.workload == "batched" else run_diff(args)
+        print(json.dumps({"workload": args.workload, "results": res}), flush=True)
     else:
         raise SystemExit(f"unknown workload {args.workload}")
 
