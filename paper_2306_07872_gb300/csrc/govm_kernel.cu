@@ -80,6 +80,8 @@ struct WarpTile {
 
 struct BlockShared {
   int32_t tprefix[kMaxInstancesPerLaunch + 1];
+  uint32_t bwords[kBlockThreads];      // bitmap words of the chunk being built
+  int32_t bstart[kBlockThreads + 1];   // rank of each word's first marked vertex
   unsigned long long scan[kWarpsPerBlock];
   unsigned long long base;
   int32_t flag;
@@ -188,91 +190,115 @@ __device__ __forceinline__ int32_t find_instance(const int32_t *tprefix, int32_t
 
 // Build delta (queue + tile table + tails_next) from beta (the bitmap) for
 // every instance; consumes (clears) the bitmap.  A block takes 256 bitmap
-// words; each warp takes 32 of them and walks them one word at a time with
-// lane l handling vertex 32 w + l, so the row_ptr and state reads of a word
-// are coalesced.  The distance key stored in an entry is read here: no
+// words, ranks their marked vertices (a popcount scan) and gives every
+// thread a contiguous run of at most kBuildPerThread ranks, so the row_ptr
+// and state reads of a round are all in flight together whatever the
+// density of the bitmap.  One atomicAdd per round reserves the entries and
+// their edge offsets.  The distance key stored in an entry is read here: no
 // relaxation runs between this phase and the next relax phase.
+constexpr int kBuildPerThread = 4;
+constexpr int kBuildRound = kBuildPerThread * kBlockThreads;
+
 __device__ void build_frontier(const GovmParams &p, unsigned long long *tails_next, BlockShared &sh,
                                unsigned long long &marked) {
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x;
   const int64_t cpi = (p.words + kBlockThreads - 1) / kBlockThreads;  // 256-word chunks per instance
   const int64_t chunks = cpi * p.k;
   for (int64_t ch = blockIdx.x; ch < chunks; ch += gridDim.x) {
     const int32_t inst = (int32_t)(ch / cpi);
-    const int64_t w0 = (ch - (int64_t)inst * cpi) * kBlockThreads + warp * 32;  // this warp's first word
+    const int64_t wbase = (ch - (int64_t)inst * cpi) * kBlockThreads;
     uint32_t *bm = p.bitmap + (size_t)inst * p.words;
-    uint32_t mine = 0;  // word w0 + lane
-    if (w0 + lane < p.words) {
-      mine = __ldcg(bm + w0 + lane);
-      if (mine) bm[w0 + lane] = 0u;
+    uint32_t bits = 0;
+    if (wbase + tid < p.words) {
+      bits = __ldcg(bm + wbase + tid);
+      if (bits) bm[wbase + tid] = 0u;
     }
-    marked += __popc(mine);
-    // pass 1: entries and edges of this warp's words
-    uint32_t cnt = 0, degsum = 0;
-    unsigned nz = __ballot_sync(kFull, mine != 0);
-    for (unsigned z = nz; z; z &= z - 1) {
-      const int i = __ffs(z) - 1;
-      const uint32_t bits = __shfl_sync(kFull, mine, i);
-      uint32_t d = 0;
-      if ((bits >> lane) & 1u) {
-        const int32_t v = (int32_t)((w0 + i) * 32 + lane);
-        d = (uint32_t)(__ldg(p.row_ptr + v + 1) - __ldg(p.row_ptr + v));
-      }
-      cnt += d > 0;
-      degsum += d;
-    }
-    unsigned long long wsum = ((unsigned long long)degsum << 32) | cnt;
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) wsum += __shfl_xor_sync(kFull, wsum, d);
-    unsigned long long total = 0;
-    const unsigned long long wexcl = block_excl_scan(lane == 0 ? wsum : 0ull, total, sh);
-    if (total == 0) continue;  // block-uniform
-    if (tid == 0) sh.base = atomicAdd(tails_next + inst, total);
+    marked += __popc(bits);
+    unsigned long long ranked = 0;
+    const int32_t start = (int32_t)block_excl_scan((unsigned long long)__popc(bits), ranked, sh);
+    if (ranked == 0) continue;  // block-uniform
+    sh.bwords[tid] = bits;
+    sh.bstart[tid] = start;
+    if (tid == 0) sh.bstart[kBlockThreads] = (int32_t)ranked;
     __syncthreads();
-    unsigned long long pos = sh.base + __shfl_sync(kFull, wexcl, 0);
-    __syncthreads();  // sh.base is rewritten by the next chunk
-    // pass 2: write the entries in (word, lane) order
+    const int32_t T = (int32_t)ranked;
     uint4 *q = p.queue + (size_t)inst * p.n;
     int32_t *tl = p.tiles + (size_t)inst * p.tiles_cap;
     const unsigned long long *st = p.state + (size_t)inst * p.n;
-    for (unsigned z = nz; z; z &= z - 1) {
-      const int i = __ffs(z) - 1;
-      const uint32_t bits = __shfl_sync(kFull, mine, i);
-      const int32_t v = (int32_t)((w0 + i) * 32 + lane);
-      uint32_t rs = 0, d = 0, key = 0;
-      if ((bits >> lane) & 1u) {
-        rs = (uint32_t)__ldg(p.row_ptr + v);
-        d = (uint32_t)__ldg(p.row_ptr + v + 1) - rs;
-        if (d > 0) key = (uint32_t)(ld_relaxed_u64(st + v) >> 32);
-      }
-      // lane prefix of (entries, edges) within this word
-      unsigned long long x = ((unsigned long long)d << 32) | (d > 0 ? 1u : 0u);
-      unsigned long long incl = x;
+    for (int32_t r0 = 0; r0 < T; r0 += kBuildRound) {  // block-uniform
+      const int32_t lo = r0 + tid * kBuildPerThread;
+      const int32_t hi = min(lo + kBuildPerThread, T);
+      int32_t v[kBuildPerThread];
+      if (lo < hi) {
+        int32_t a = 0, b = kBlockThreads;  // word holding rank lo: largest w with bstart[w] <= lo
+        while (b - a > 1) {
+          const int32_t mid = (a + b) >> 1;
+          if (sh.bstart[mid] <= lo) a = mid; else b = mid;
+        }
+        int32_t w = a;
+        uint32_t m = sh.bwords[w];
+        for (int32_t skip = lo - sh.bstart[w]; skip > 0; --skip) m &= m - 1;
 #pragma unroll
-      for (int s = 1; s < 32; s <<= 1) {
-        const unsigned long long o = __shfl_up_sync(kFull, incl, s);
-        if (lane >= s) incl += o;
-      }
-      if (d > 0) {
-        const unsigned long long at = pos + incl - x;
-        const uint32_t idx = (uint32_t)at;
-        const uint32_t off = (uint32_t)(at >> 32);
-        if (idx >= (uint32_t)p.n) {  // cannot happen: each vertex has one bit
-          set_status(p.ctl, DAWN_ERR_BOUNDS);
-        } else {
-          q[idx] = make_uint4(rs, off, key, (uint32_t)v);
-          const uint32_t end = off + d;
-          for (uint32_t tb = (off + kTile - 1) / kTile; tb * (uint32_t)kTile < end; ++tb) {
-            if (tb >= (uint32_t)p.tiles_cap) {
+        for (int i = 0; i < kBuildPerThread; ++i) {
+          v[i] = -1;
+          if (lo + i < hi) {
+            while (m == 0 && w + 1 < kBlockThreads) m = sh.bwords[++w];
+            if (m == 0) {  // cannot happen: every rank below T has a marked bit
               set_status(p.ctl, DAWN_ERR_BOUNDS);
               break;
             }
-            tl[tb] = (int32_t)idx;
+            v[i] = (int32_t)((wbase + w) * 32 + __ffs(m) - 1);
+            m &= m - 1;
           }
         }
+      } else {
+#pragma unroll
+        for (int i = 0; i < kBuildPerThread; ++i) v[i] = -1;
       }
-      pos += __shfl_sync(kFull, incl, 31);
+      uint32_t rs[kBuildPerThread], d[kBuildPerThread], key[kBuildPerThread];
+#pragma unroll
+      for (int i = 0; i < kBuildPerThread; ++i) {
+        rs[i] = v[i] >= 0 ? (uint32_t)__ldg(p.row_ptr + v[i]) : 0u;
+        d[i] = v[i] >= 0 ? (uint32_t)__ldg(p.row_ptr + v[i] + 1) : 0u;
+        key[i] = v[i] >= 0 ? (uint32_t)(ld_relaxed_u64(st + v[i]) >> 32) : 0u;
+      }
+      uint32_t cnt = 0, degsum = 0;
+#pragma unroll
+      for (int i = 0; i < kBuildPerThread; ++i) {
+        d[i] -= rs[i];
+        cnt += d[i] > 0;
+        degsum += d[i];
+      }
+      unsigned long long total = 0;
+      const unsigned long long excl = block_excl_scan(((unsigned long long)degsum << 32) | cnt, total, sh);
+      if (total == 0) continue;  // block-uniform
+      if (tid == 0) sh.base = atomicAdd(tails_next + inst, total);
+      __syncthreads();
+      const unsigned long long pos = sh.base + excl;
+      __syncthreads();  // sh.base is rewritten by the next round
+      uint32_t idx = (uint32_t)pos;
+      uint32_t off = (uint32_t)(pos >> 32);
+#pragma unroll
+      for (int i = 0; i < kBuildPerThread; ++i) {
+        if (d[i] == 0) continue;
+        if (idx >= (uint32_t)p.n) {  // cannot happen: each vertex has one bit
+          set_status(p.ctl, DAWN_ERR_BOUNDS);
+          break;
+        }
+        q[idx] = make_uint4(rs[i], off, key[i], (uint32_t)v[i]);
+        const uint32_t end = off + d[i];
+        for (uint32_t tb = (off + kTile - 1) / kTile; tb * (uint32_t)kTile < end; ++tb) {
+          if (tb >= (uint32_t)p.tiles_cap) {
+            set_status(p.ctl, DAWN_ERR_BOUNDS);
+            break;
+          }
+          tl[tb] = (int32_t)idx;
+        }
+        ++idx;
+        off = end;
+      }
     }
+    __syncthreads();  // bwords / bstart are rewritten by the next chunk
   }
 }
 
