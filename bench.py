@@ -52,6 +52,37 @@ def measured_peak():
         return HBM_FALLBACK_GBS, "fallback"
 
 
+KERNEL_SOURCES = ("paper_2306_07872_gb300/csrc/govm_kernel.cu", "paper_2306_07872_gb300/csrc/dawn_common.cuh")
+TRAFFIC_SUMMARY = "profiles/govm_kernel_rmat22_traffic.md"
+
+
+def kernel_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(workload: str):
+    """Per-launch DRAM bytes of govm_kernel from the committed ncu summary,
+    or None when the summary is missing, is for another workload, or was taken
+    on a different version of the kernel sources."""
+    try:
+        with open(os.path.join(ROOT, TRAFFIC_SUMMARY)) as f:
+            kv = dict(l.split(":", 1) for l in f.read().splitlines() if l.startswith("- ") and ":" in l)
+    except OSError:
+        return None
+    kv = {k[2:].strip(): v.strip().strip("`") for k, v in kv.items()}
+    if kv.get("kernel_source_sha256_16") != kernel_hash() or kv.get("workload") != workload:
+        return None
+    try:
+        return float(kv["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -488,7 +519,7 @@ def main_ours(args):
                        "l2": "inputs larger than L2 (CSR col+w %.0f MB > 129 MB); no flush" %
                              ((wl.col.nbytes + wl.weights.nbytes) / 1e6)},
             "roofline": {"bound": "hbm", "achieved": res["achieved_gbs"], "peak": peak, "unit": "GB/s",
-                         "frac": res["achieved_gbs"] / peak, "traffic": None,
+                         "frac": res["achieved_gbs"] / peak, "traffic": recorded_traffic(wl.name),
                          "peak_kind": f"{peak_kind} copy bandwidth", "kernel": "govm_kernel",
                          "b_alg_per_launch": res["b_alg_mean"], "launch_ms": res["launch_ms_mean"],
                          "frac_of_8000": res["achieved_gbs"] / 8000.0},
