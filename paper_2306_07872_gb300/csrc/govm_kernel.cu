@@ -80,8 +80,6 @@ struct WarpTile {
 
 struct BlockShared {
   int32_t tprefix[kMaxInstancesPerLaunch + 1];
-  uint32_t bwords[kBlockThreads];      // bitmap words of the chunk being built
-  int32_t bstart[kBlockThreads + 1];   // rank of each word's first marked vertex
   unsigned long long scan[kWarpsPerBlock];
   unsigned long long base;
   int32_t flag;
@@ -151,6 +149,16 @@ __device__ __forceinline__ unsigned long long block_excl_scan(unsigned long long
 // frontier (tiles = ceil(edges / kTile)).  Returns the total.
 __device__ int32_t scan_tiles(const unsigned long long *tails_cur, int32_t k, BlockShared &sh) {
   const int tid = threadIdx.x;
+  if (k == 1) {  // one instance: no prefix needed
+    const uint32_t e = (uint32_t)(__ldcg(tails_cur) >> 32);
+    const int32_t t = (int32_t)((e + kTile - 1) / kTile);
+    // every thread stores the same two values before reading them; the
+    // device-wide barrier that ended the previous phase already ordered the
+    // previous step's readers before these stores
+    sh.tprefix[0] = 0;
+    sh.tprefix[1] = t;
+    return t;
+  }
   constexpr int kPer = kMaxInstancesPerLaunch / kBlockThreads;
   int32_t vals[kPer];
   int32_t sum = 0;
@@ -189,97 +197,110 @@ __device__ __forceinline__ int32_t find_instance(const int32_t *tprefix, int32_t
 }
 
 // Build delta (queue + tile table + tails_next) from beta (the bitmap) for
-// every instance; consumes (clears) the bitmap.  A block takes 256 bitmap
-// words, ranks their marked vertices (a popcount scan) and gives every
-// thread a contiguous run of at most kBuildPerThread ranks, so the row_ptr
-// and state reads of a round are all in flight together whatever the
-// density of the bitmap.  One atomicAdd per round reserves the entries and
-// their edge offsets.  The distance key stored in an entry is read here: no
-// relaxation runs between this phase and the next relax phase.
-constexpr int kBuildPerThread = 4;
-constexpr int kBuildRound = kBuildPerThread * kBlockThreads;
+// every instance; consumes (clears) the bitmap.  Work is split into 32-word
+// chunks (1024 vertices) handed to warps round-robin; a warp ranks the marked
+// vertices of its chunk with a popcount scan and expands them in rounds of
+// 128 (four consecutive ranks per lane), so all row_ptr and state reads of a
+// round are in flight together and no block-wide synchronisation is needed.
+// One atomicAdd per round reserves the entries and their edge offsets.  The
+// distance key stored in an entry is read here: no relaxation runs between
+// this phase and the next relax phase.
+constexpr int kBuildPerLane = 4;
 
-__device__ void build_frontier(const GovmParams &p, unsigned long long *tails_next, BlockShared &sh,
+__device__ void build_frontier(const GovmParams &p, unsigned long long *tails_next, WarpTile &wt,
                                unsigned long long &marked) {
-  const int tid = threadIdx.x;
-  const int64_t cpi = (p.words + kBlockThreads - 1) / kBlockThreads;  // 256-word chunks per instance
+  const int lane = threadIdx.x & 31;
+  const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t cpi = (p.words + 31) / 32;  // 32-word chunks per instance
   const int64_t chunks = cpi * p.k;
-  for (int64_t ch = blockIdx.x; ch < chunks; ch += gridDim.x) {
+  uint32_t *wbits = wt.rs;            // the relax tile buffers are free during the build
+  uint32_t *wstart = wt.off;
+  for (int64_t ch = gwarp; ch < chunks; ch += nwarps) {
     const int32_t inst = (int32_t)(ch / cpi);
-    const int64_t wbase = (ch - (int64_t)inst * cpi) * kBlockThreads;
+    const int64_t w0 = (ch - (int64_t)inst * cpi) * 32;
     uint32_t *bm = p.bitmap + (size_t)inst * p.words;
     uint32_t bits = 0;
-    if (wbase + tid < p.words) {
-      bits = __ldcg(bm + wbase + tid);
-      if (bits) bm[wbase + tid] = 0u;
+    if (w0 + lane < p.words) {
+      bits = __ldcg(bm + w0 + lane);
+      if (bits) bm[w0 + lane] = 0u;
     }
-    marked += __popc(bits);
-    unsigned long long ranked = 0;
-    const int32_t start = (int32_t)block_excl_scan((unsigned long long)__popc(bits), ranked, sh);
-    if (ranked == 0) continue;  // block-uniform
-    sh.bwords[tid] = bits;
-    sh.bstart[tid] = start;
-    if (tid == 0) sh.bstart[kBlockThreads] = (int32_t)ranked;
-    __syncthreads();
-    const int32_t T = (int32_t)ranked;
+    const uint32_t pc = __popc(bits);
+    marked += pc;
+    uint32_t incl = pc;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t o = __shfl_up_sync(kFull, incl, d);
+      if (lane >= d) incl += o;
+    }
+    const uint32_t T = __shfl_sync(kFull, incl, 31);
+    if (T == 0) continue;  // warp-uniform
+    __syncwarp();
+    wbits[lane] = bits;
+    wstart[lane] = incl - pc;
+    __syncwarp();
     uint4 *q = p.queue + (size_t)inst * p.n;
     int32_t *tl = p.tiles + (size_t)inst * p.tiles_cap;
     const unsigned long long *st = p.state + (size_t)inst * p.n;
-    for (int32_t r0 = 0; r0 < T; r0 += kBuildRound) {  // block-uniform
-      const int32_t lo = r0 + tid * kBuildPerThread;
-      const int32_t hi = min(lo + kBuildPerThread, T);
-      int32_t v[kBuildPerThread];
+    for (uint32_t r0 = 0; r0 < T; r0 += 32 * kBuildPerLane) {  // warp-uniform
+      const uint32_t lo = r0 + lane * kBuildPerLane;
+      const uint32_t hi = min(lo + kBuildPerLane, T);
+      int32_t v[kBuildPerLane];
+#pragma unroll
+      for (int i = 0; i < kBuildPerLane; ++i) v[i] = -1;
       if (lo < hi) {
-        int32_t a = 0, b = kBlockThreads;  // word holding rank lo: largest w with bstart[w] <= lo
+        int32_t a = 0, b = 32;  // word holding rank lo: largest w with wstart[w] <= lo
         while (b - a > 1) {
           const int32_t mid = (a + b) >> 1;
-          if (sh.bstart[mid] <= lo) a = mid; else b = mid;
+          if (wstart[mid] <= lo) a = mid; else b = mid;
         }
         int32_t w = a;
-        uint32_t m = sh.bwords[w];
-        for (int32_t skip = lo - sh.bstart[w]; skip > 0; --skip) m &= m - 1;
+        uint32_t m = wbits[w];
+        for (uint32_t skip = lo - wstart[w]; skip > 0; --skip) m &= m - 1;
 #pragma unroll
-        for (int i = 0; i < kBuildPerThread; ++i) {
-          v[i] = -1;
+        for (int i = 0; i < kBuildPerLane; ++i) {
           if (lo + i < hi) {
-            while (m == 0 && w + 1 < kBlockThreads) m = sh.bwords[++w];
+            while (m == 0 && w + 1 < 32) m = wbits[++w];
             if (m == 0) {  // cannot happen: every rank below T has a marked bit
               set_status(p.ctl, DAWN_ERR_BOUNDS);
               break;
             }
-            v[i] = (int32_t)((wbase + w) * 32 + __ffs(m) - 1);
+            v[i] = (int32_t)((w0 + w) * 32 + __ffs(m) - 1);
             m &= m - 1;
           }
         }
-      } else {
-#pragma unroll
-        for (int i = 0; i < kBuildPerThread; ++i) v[i] = -1;
       }
-      uint32_t rs[kBuildPerThread], d[kBuildPerThread], key[kBuildPerThread];
+      uint32_t rs[kBuildPerLane], d[kBuildPerLane], key[kBuildPerLane];
 #pragma unroll
-      for (int i = 0; i < kBuildPerThread; ++i) {
+      for (int i = 0; i < kBuildPerLane; ++i) {
         rs[i] = v[i] >= 0 ? (uint32_t)__ldg(p.row_ptr + v[i]) : 0u;
         d[i] = v[i] >= 0 ? (uint32_t)__ldg(p.row_ptr + v[i] + 1) : 0u;
         key[i] = v[i] >= 0 ? (uint32_t)(ld_relaxed_u64(st + v[i]) >> 32) : 0u;
       }
       uint32_t cnt = 0, degsum = 0;
 #pragma unroll
-      for (int i = 0; i < kBuildPerThread; ++i) {
+      for (int i = 0; i < kBuildPerLane; ++i) {
         d[i] -= rs[i];
         cnt += d[i] > 0;
         degsum += d[i];
       }
-      unsigned long long total = 0;
-      const unsigned long long excl = block_excl_scan(((unsigned long long)degsum << 32) | cnt, total, sh);
-      if (total == 0) continue;  // block-uniform
-      if (tid == 0) sh.base = atomicAdd(tails_next + inst, total);
-      __syncthreads();
-      const unsigned long long pos = sh.base + excl;
-      __syncthreads();  // sh.base is rewritten by the next round
+      const unsigned long long mine = ((unsigned long long)degsum << 32) | cnt;
+      unsigned long long pre = mine;
+#pragma unroll
+      for (int s2 = 1; s2 < 32; s2 <<= 1) {
+        const unsigned long long o = __shfl_up_sync(kFull, pre, s2);
+        if (lane >= s2) pre += o;
+      }
+      const unsigned long long total = __shfl_sync(kFull, pre, 31);
+      if (total == 0) continue;  // warp-uniform
+      unsigned long long base = 0;
+      if (lane == 31) base = atomicAdd(tails_next + inst, total);
+      base = __shfl_sync(kFull, base, 31);
+      const unsigned long long pos = base + pre - mine;
       uint32_t idx = (uint32_t)pos;
       uint32_t off = (uint32_t)(pos >> 32);
 #pragma unroll
-      for (int i = 0; i < kBuildPerThread; ++i) {
+      for (int i = 0; i < kBuildPerLane; ++i) {
         if (d[i] == 0) continue;
         if (idx >= (uint32_t)p.n) {  // cannot happen: each vertex has one bit
           set_status(p.ctl, DAWN_ERR_BOUNDS);
@@ -298,7 +319,6 @@ __device__ void build_frontier(const GovmParams &p, unsigned long long *tails_ne
         off = end;
       }
     }
-    __syncthreads();  // bwords / bstart are rewritten by the next chunk
   }
 }
 
@@ -464,7 +484,7 @@ __global__ void __launch_bounds__(kBlockThreads, 5) govm_kernel(GovmParams p) {
     atomicOr(p.bitmap + (size_t)inst * p.words + (s >> 5), 1u << (s & 31));
   }
   if (!grid_barrier(ctl, p.wait_limit_ns, &sh.flag)) goto finish;
-  build_frontier(p, p.tails, sh, seeded);
+  build_frontier(p, p.tails, sh.wt[warp], seeded);
   if (!grid_barrier(ctl, p.wait_limit_ns, &sh.flag)) goto finish;
 
   // 3. GOVM steps.
@@ -510,7 +530,7 @@ __global__ void __launch_bounds__(kBlockThreads, 5) govm_kernel(GovmParams p) {
     }
     if (!grid_barrier(ctl, p.wait_limit_ns, &sh.flag)) break;
     // build the next frontier
-    build_frontier(p, tails_next, sh, updates);
+    build_frontier(p, tails_next, sh.wt[warp], updates);
     if (!grid_barrier(ctl, p.wait_limit_ns, &sh.flag)) break;
   }
 
