@@ -46,6 +46,16 @@ __device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+__device__ __forceinline__ unsigned atom_add_acq_rel_u32(unsigned *p, unsigned v) {
+  unsigned o;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(o) : "l"(p), "r"(v) : "memory");
+  return o;
+}
+
+__device__ __forceinline__ void st_relaxed_u32(unsigned *p, unsigned v) {
+  asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 __device__ __forceinline__ int ld_volatile_i32(const int *p) { return *(volatile const int *)p; }
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -89,16 +99,18 @@ struct BlockShared {
 __device__ __forceinline__ void set_status(DeviceCtl *ctl, int code) { atomicCAS(&ctl->status, 0, code); }
 
 // Device-wide barrier with a bounded wait.  Returns false (uniformly for the
-// block) when the status word reports an error or the wait ran out.
+// block) when the status word reports an error or the wait ran out.  The
+// arrival is an acquire-release add (it publishes the block's writes, ordered
+// before it by the block barrier); the last arrival resets the counter and
+// publishes the new generation with a release store that every waiter
+// acquires.
 __device__ bool grid_barrier(DeviceCtl *ctl, unsigned long long limit_ns, int32_t *s_flag) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    unsigned gen = ld_acquire_u32(&ctl->bar_gen);
-    __threadfence();
-    unsigned arrived = atomicAdd(&ctl->bar_count, 1u);
+    const unsigned gen = ld_acquire_u32(&ctl->bar_gen);
+    const unsigned arrived = atom_add_acq_rel_u32(&ctl->bar_count, 1u);
     if (arrived == gridDim.x - 1) {
-      atomicExch(&ctl->bar_count, 0u);
-      __threadfence();
+      st_relaxed_u32(&ctl->bar_count, 0u);
       st_release_u32(&ctl->bar_gen, gen + 1);
     } else {
       unsigned long long t0 = global_ns();
@@ -113,7 +125,6 @@ __device__ bool grid_barrier(DeviceCtl *ctl, unsigned long long limit_ns, int32_
         if (ns < 128) ns <<= 1;
       }
     }
-    __threadfence();
     *s_flag = ld_volatile_i32(&ctl->status) == 0;
   }
   __syncthreads();
