@@ -422,11 +422,16 @@ def run_diff(args):
     grad_dist[tg] = cf
     grad_w = torch.empty(wl.m, dtype=torch.float32, device="cuda")
     t_bwd = _time(lambda: dawn.dawn_sssp_backward(g.handle, pe, grad_dist, grad_w), reps=20, warm=3)
+    def c_abi_fwd_bwd():
+        dawn.dawn_sssp(g.handle, 0, dist, None, pe)
+        dawn.dawn_sssp_backward(g.handle, pe, grad_dist, grad_w)
+    t_cfb = _time(c_abi_fwd_bwd, reps=20, warm=3)
     g.check()
     g.close()
-    return {"diff_rmat16_f32": {"plain_sssp_s": t_plain, "forward_s": t_fwd, "forward_backward_s": t_fb,
-                                "backward_kernel_s": t_bwd, "fb_over_plain": t_fb / t_plain,
-                                "n": wl.n, "m": wl.m}}
+    return {"diff_rmat16_f32": {"plain_sssp_s": t_plain, "c_abi_forward_backward_s": t_cfb,
+                                "c_abi_fb_over_plain": t_cfb / t_plain, "backward_kernel_s": t_bwd,
+                                "autograd_forward_s": t_fwd, "autograd_forward_backward_s": t_fb,
+                                "autograd_fb_over_plain": t_fb / t_plain, "n": wl.n, "m": wl.m}}
 
 
 # ----------------------------------------------------------------- plumbing

@@ -105,6 +105,12 @@ __device__ __forceinline__ void set_status(DeviceCtl *ctl, int code) { atomicCAS
 // publishes the new generation with a release store that every waiter
 // acquires.
 __device__ bool grid_barrier(DeviceCtl *ctl, unsigned long long limit_ns, int32_t *s_flag) {
+  if (gridDim.x == 1) {  // one block: the block barrier already orders its memory operations
+    __syncthreads();
+    if (threadIdx.x == 0) *s_flag = ld_volatile_i32(&ctl->status) == 0;
+    __syncthreads();
+    return *s_flag != 0;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
     const unsigned gen = ld_acquire_u32(&ctl->bar_gen);
