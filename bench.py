@@ -434,6 +434,77 @@ def run_diff(args):
                                 "autograd_fb_over_plain": t_fb / t_plain, "n": wl.n, "m": wl.m}}
 
 
+def run_mu(args):
+    """The paper's validation experiment (Section 4.2) on synthetic graphs:
+    every graph is solved with all weights 1.0f and with fp32 weights
+    uniform in [0, 2]; mu = path updates / (reached vertices - 1) on the GPU
+    (vertices entering beta per step) and, for one source, from the literal
+    Algorithm 2 in the oracle.  With unit weights mu is exactly 1; the
+    difference is the share of paths that GOVM had to update."""
+    import torch
+    import graphgen as gg
+    import oracle
+    import paper_2306_07872_gb300 as dawn
+    graphs = {
+        "rmat_s18": lambda: gg.rmat(18, 16, seed=0, relabel=True),
+        "er_n262144_d16": lambda: gg.erdos_renyi(1 << 18, 16 << 18, seed=3),
+        "grid_512": lambda: gg.grid(512, 0.01, seed=1)[:2],
+    }
+    out = {}
+    for name, make in graphs.items():
+        rp, cl = make()
+        src, _, e_wcc = gg.wcc_sources(rp, cl, 4, seed=5)
+        res = {}
+        for wname, w in (("unit", np.ones(len(cl), np.float32)),
+                         ("u02", gg.weights_f32_uniform(len(cl), 0.0, 2.0, seed=9))):
+            g = dawn.Graph(rp, cl, w)
+            mus, times = [], []
+            for s_ in src:
+                dist, _, _ = g.sssp(int(s_), parent=False)
+                t = _time(lambda: g.sssp(int(s_), parent=False, check=False), reps=3, warm=1)
+                st = g.stats()
+                reached = int(torch.isfinite(dist).sum().item())
+                mus.append(st["updates"] / max(reached - 1, 1))
+                times.append(t)
+            _, ost = oracle.govm(rp, cl, w, int(src[0]))
+            res[wname] = {"mu_gpu": float(np.mean(mus)), "mu_oracle_alg2": ost["mu"], "solve_ms": 1e3 * float(np.mean(times))}
+            g.close()
+        res["updated_path_ratio_gpu"] = res["u02"]["mu_gpu"] - 1.0
+        res["updated_path_ratio_oracle"] = res["u02"]["mu_oracle_alg2"] - 1.0
+        res["time_ratio_u02_over_unit"] = res["u02"]["solve_ms"] / res["unit"]["solve_ms"]
+        out[name] = res
+    return out
+
+
+def run_apsp(args):
+    """APSP as repeated SSSP (Section 3.4): every vertex of an R-MAT scale-14
+    graph is a source, solved in batched launches of up to 1024 instances
+    (dawn_msssp); the paper's work bound is mu * S_wcc * E_wcc edge
+    relaxations."""
+    import torch
+    import graphgen as gg
+    import paper_2306_07872_gb300 as dawn
+    scale = 14
+    rp, cl = gg.rmat(scale, 16, seed=0, relabel=True)
+    w = gg.weights_u32(len(cl), 1, 255, seed=1)
+    _, s_wcc, e_wcc = gg.largest_wcc(rp, cl)
+    n = len(rp) - 1
+    g = dawn.Graph(rp, cl, w)
+    src = torch.arange(n, dtype=torch.int32, device="cuda")
+    dist = torch.empty((n, n), dtype=torch.uint32, device="cuda")
+    t = _time(lambda: dawn.dawn_msssp(g.handle, src, dist, None), reps=2, warm=1)
+    g.check()
+    # work: per-chunk counters summed (the stats describe the last chunk; re-run chunk by chunk)
+    scanned = 0
+    for b in range(0, n, 1024):
+        dawn.dawn_msssp(g.handle, src[b:b + 1024], dist[b:b + 1024], None)
+        scanned += g.stats()["edges_scanned"]
+    g.close()
+    return {"apsp_rmat14": {"n": n, "m": len(cl), "s_wcc": s_wcc, "e_wcc": e_wcc, "seconds": t,
+                            "gteps": n * e_wcc / t / 1e9, "edges_scanned": scanned,
+                            "mu_work": scanned / (s_wcc * e_wcc)}}
+
+
 # ----------------------------------------------------------------- plumbing
 
 def barrier(world):
@@ -535,10 +606,10 @@ def main_ours(args):
             "e2e": e2e, "gpu_launches": res["launches"], "clocks": res["clocks"], "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
-    elif args.workload in ("batched", "diff"):
+    elif args.workload in ("batched", "diff", "mu", "apsp"):
         if world > 1 and rank != 0:
             return
-        res = run_batched(args) if args.workload == "batched" else run_diff(args)
+        res = {"batched": run_batched, "diff": run_diff, "mu": run_mu, "apsp": run_apsp}[args.workload](args)
         print(json.dumps({"workload": args.workload, "results": res}), flush=True)
     else:
         raise SystemExit(f"unknown workload {args.workload}")

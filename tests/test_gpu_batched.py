@@ -64,6 +64,21 @@ def test_apsp_small(dawn):
     assert np.array_equal(dist.cpu().numpy().view(np.uint32), D.view(np.uint32))
 
 
+def test_apsp_medium_sampled_rows(dawn):
+    # all 4096 sources of an ER graph in chunked batched launches; sampled
+    # rows bit-exact to Dijkstra, every sampled row certified
+    wl = gg.tiny_er(n=4096, avg_deg=8, seed=11)
+    g = dawn.Graph(wl.row_ptr, wl.col, wl.weights)
+    dist, par = g.msssp(np.arange(wl.n, dtype=np.int32))
+    dist = dist.cpu().numpy()
+    par = par.cpu().numpy()
+    for s in range(0, wl.n, 257):
+        d_ref = oracle.dijkstra(wl.row_ptr, wl.col, wl.weights, s)
+        assert np.array_equal(dist[s], d_ref), s
+        pe = oracle.parent_edges(wl.row_ptr, wl.col, wl.weights, s, d_ref)
+        assert np.array_equal(par[s], oracle.parent_vertices(wl.row_ptr, s, d_ref, pe, "u32")), s
+
+
 def test_roots_on_uneven_batch(dawn):
     wl = gg.er_batch(count=12, nlo=100, nhi=20000, dlo=4, dhi=32, seed=6)
     g = dawn.Graph(wl.row_ptr, wl.col, wl.weights)

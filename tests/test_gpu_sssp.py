@@ -91,6 +91,19 @@ def test_rmat_f32_exact(dawn):
     assert_exact(wl.row_ptr, wl.col, wl.weights, 0, d, p, pe)
 
 
+def test_rmat_f32_weights_down_to_zero_exact(dawn):
+    # the paper's comparative weights (Section 4.2): fp32 uniform in [0, 2];
+    # tiny weights make fl(d + w) == d ties, which the parent rule resolves
+    rp, cl = gg.rmat(12, 16, seed=4)
+    w = gg.weights_f32_uniform(len(cl), 0.0, 2.0, seed=8)
+    w[::97] = np.float32(0.0)
+    g = dawn.Graph(rp, cl, w)
+    src, _, _ = gg.wcc_sources(rp, cl, 3, seed=2)
+    for s in src:
+        d, p, pe = solve(g, int(s))
+        assert_exact(rp, cl, w, int(s), d, p, pe)
+
+
 def test_unit_weights_bfs_and_mu_one(dawn):
     # Section 4.2: unit weights find every path once (mu = 1)
     wl = gg.rmat_u32(13, 8, nsrc=2, seed=7, wlo=1, whi=1)
