@@ -505,6 +505,31 @@ def run_apsp(args):
                             "mu_work": scanned / (s_wcc * e_wcc)}}
 
 
+def run_gsvm(args):
+    """Ablation of GOVM's frontier (Section 3.4) against GSVM (Algorithm 1,
+    Section 3.2), both on the GPU: time, steps and edges relaxed per solve."""
+    import graphgen as gg
+    import paper_2306_07872_gb300 as dawn
+    out = {}
+    for name, wl in (("rmat_s20", gg.rmat_u32(20, 16, nsrc=4, seed=0)), ("grid_512", gg.grid_f32(512, 0.01, nsrc=4, seed=0))):
+        g = dawn.Graph(wl.row_ptr, wl.col, wl.weights)
+        res = {}
+        for alg, flag in (("govm", 0), ("gsvm", 1)):
+            g.set_option(dawn.DAWN_OPT_GSVM, flag)
+            ts, st = [], []
+            for s_ in wl.sources:
+                ts.append(_time(lambda: g.sssp(int(s_), parent=False, check=False), reps=3, warm=1))
+                g.check()
+                st.append(g.stats())
+            res[alg] = {"solve_ms": 1e3 * float(np.mean(ts)), "steps": float(np.mean([x["steps"] for x in st])),
+                        "edges_scanned": float(np.mean([x["edges_scanned"] for x in st]))}
+        res["work_ratio_gsvm_over_govm"] = res["gsvm"]["edges_scanned"] / res["govm"]["edges_scanned"]
+        res["time_ratio_gsvm_over_govm"] = res["gsvm"]["solve_ms"] / res["govm"]["solve_ms"]
+        out[name] = res
+        g.close()
+    return out
+
+
 # ----------------------------------------------------------------- plumbing
 
 def barrier(world):
@@ -606,10 +631,11 @@ def main_ours(args):
             "e2e": e2e, "gpu_launches": res["launches"], "clocks": res["clocks"], "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
-    elif args.workload in ("batched", "diff", "mu", "apsp"):
+    elif args.workload in ("batched", "diff", "mu", "apsp", "gsvm"):
         if world > 1 and rank != 0:
             return
-        res = {"batched": run_batched, "diff": run_diff, "mu": run_mu, "apsp": run_apsp}[args.workload](args)
+        res = {"batched": run_batched, "diff": run_diff, "mu": run_mu, "apsp": run_apsp,
+               "gsvm": run_gsvm}[args.workload](args)
         print(json.dumps({"workload": args.workload, "results": res}), flush=True)
     else:
         raise SystemExit(f"unknown workload {args.workload}")

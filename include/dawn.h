@@ -181,13 +181,20 @@ int dawn_get_stats(dawn_graph g, dawn_stats *out);
  *                          bounded waits run out (tests DAWN_ERR_TIMEOUT)
  *   DAWN_OPT_TRACE_STEPS   record up to `value` per-step trace rows in later
  *                          solves (0 = off, the default); allocates
+ *   DAWN_OPT_GSVM          1: solve with Algorithm 1 (GSVM, Section 3.2) instead
+ *                          of Algorithm 2: every step rescans the out-edges of
+ *                          every reached vertex and the loop stops after a
+ *                          step that changes no path (same distances, more
+ *                          work; an ablation of GOVM's frontier).  In this mode
+ *                          dawn_stats.updates counts expanded vertices.
  */
 enum {
   DAWN_OPT_MAX_STEPS = 1,
   DAWN_OPT_WAIT_LIMIT_NS = 2,
   DAWN_OPT_GRID_BLOCKS = 3,
   DAWN_OPT_TEST_STALL = 4,
-  DAWN_OPT_TRACE_STEPS = 5
+  DAWN_OPT_TRACE_STEPS = 5,
+  DAWN_OPT_GSVM = 6
 };
 int dawn_set_option(dawn_graph g, int option, int64_t value);
 

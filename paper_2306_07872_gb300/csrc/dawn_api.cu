@@ -42,6 +42,7 @@ struct dawn_graph_s {
   unsigned long long wait_limit_ns = 4000000000ull;
   int grid_blocks = 0;
   int test_stall = 0;
+  int gsvm = 0;
   int blocks_per_sm = 0;  // co-resident persistent blocks per SM (cached)
   int last_k = 0;
   cudaStream_t last_stream = nullptr;
@@ -245,6 +246,7 @@ int run_solve(dawn_graph g, const int32_t *seeds, int32_t nseeds, int32_t source
   p.max_steps = g->max_steps > 0 ? g->max_steps : g->n;
   p.wait_limit_ns = g->wait_limit_ns;
   p.test_stall = g->test_stall;
+  p.gsvm = g->gsvm;
   p.trace = g->trace;
   p.trace_cap = g->trace_cap;
   cudaError_t e = cudaMemsetAsync(g->ctl, 0, sizeof(DeviceCtl), stream);
@@ -472,6 +474,7 @@ int dawn_set_option(dawn_graph g, int option, int64_t value) {
       g->grid_blocks = (int)value;
       return DAWN_OK;
     case DAWN_OPT_TEST_STALL: g->test_stall = value != 0; return DAWN_OK;
+    case DAWN_OPT_GSVM: g->gsvm = value != 0; return DAWN_OK;
     case DAWN_OPT_TRACE_STEPS: {
       if (value < 0 || value > (1 << 24)) return DAWN_ERR_INVALID;
       if (set_device(g)) return DAWN_ERR_CUDA;

@@ -49,6 +49,7 @@ struct DeviceCtl {
   unsigned long long frontier_sum;
   unsigned long long edges_scanned;
   unsigned long long updates;
+  unsigned int changed[3];  // Algorithm 1 only: "a path changed in step t" flags, t mod 3
 };
 
 struct GovmParams {
@@ -76,6 +77,7 @@ struct GovmParams {
   int64_t max_steps;
   unsigned long long wait_limit_ns;
   int test_stall;
+  int gsvm;                  // 1: run Algorithm 1 (rescan every reached vertex each step)
   unsigned long long *trace;  // optional per-step trace [trace_cap][4], null when off
   int32_t trace_cap;
 };

@@ -240,7 +240,7 @@ __device__ void build_frontier(const GovmParams &p, unsigned long long *tails_ne
     uint32_t bits = 0;
     if (w0 + lane < p.words) {
       bits = __ldcg(bm + w0 + lane);
-      if (bits) bm[w0 + lane] = 0u;
+      if (bits && !p.gsvm) bm[w0 + lane] = 0u;  // Algorithm 1 keeps every reached vertex
     }
     const uint32_t pc = __popc(bits);
     marked += pc;
@@ -342,7 +342,7 @@ __device__ void build_frontier(const GovmParams &p, unsigned long long *tails_ne
 // Relax the out-edges in virtual-edge tile t of instance inst's frontier.
 template <bool F32>
 __device__ __forceinline__ void relax_tile(const GovmParams &p, WarpTile &wt, int32_t inst, int32_t t,
-                                           unsigned long long tail_cur, int32_t tiles_i) {
+                                           unsigned long long tail_cur, int32_t tiles_i, unsigned *changed) {
   const int lane = threadIdx.x & 31;
   const uint32_t E = (uint32_t)(tail_cur >> 32);
   const int32_t c = (int32_t)(uint32_t)tail_cur;
@@ -442,14 +442,20 @@ __device__ __forceinline__ void relax_tile(const GovmParams &p, WarpTile &wt, in
     if ((valid & (1u << r)) && cand < curst[r] && curst[r] != kSourceState) need |= 1u << r;
   }
   // Both atomics are fire-and-forget reductions: nothing waits for them.
+  unsigned strict = 0;
 #pragma unroll
   for (int r = 0; r < kEdgesPerLane; ++r) {
     if (need & (1u << r)) {
       const uint32_t t = cw[r].x;
-      if (ckey[r] < (uint32_t)(curst[r] >> 32)) atomicOr(bm + (t >> 5), 1u << (t & 31));
+      if (ckey[r] < (uint32_t)(curst[r] >> 32)) {
+        atomicOr(bm + (t >> 5), 1u << (t & 31));
+        strict |= 1u << r;
+      }
       atomicMin(st + t, ((unsigned long long)ckey[r] << 32) | eidx[r]);
     }
   }
+  // Algorithm 1's "ptr": some path changed in this step
+  if (changed && __any_sync(kFull, strict != 0) && lane == 0) atomicOr(changed, 1u);
 }
 
 template <bool F32>
@@ -513,6 +519,12 @@ __global__ void __launch_bounds__(kBlockThreads, 5) govm_kernel(GovmParams p) {
       quiescent = true;
       break;
     }
+    // Algorithm 1 stops after a step in which no path changed (its frontier,
+    // every reached vertex, never empties)
+    if (p.gsvm && step > 0 && ld_volatile_i32((const int *)&ctl->changed[(step - 1) % 3]) == 0) {
+      quiescent = true;
+      break;
+    }
     if (step >= p.max_steps) {
       if (gtid == 0) set_status(ctl, DAWN_ERR_NOT_CONVERGED);
       quiescent = true;
@@ -536,6 +548,7 @@ __global__ void __launch_bounds__(kBlockThreads, 5) govm_kernel(GovmParams p) {
       }
       if (fs) atomicAdd(&ctl->frontier_sum, fs);
       if (es) atomicAdd(&ctl->edges_scanned, es);
+      if (tid == 0) ctl->changed[(step + 1) % 3] = 0u;  // read two steps from now
     }
     // relax
     const int32_t gw = blockIdx.x * kWarpsPerBlock + warp;
@@ -543,7 +556,7 @@ __global__ void __launch_bounds__(kBlockThreads, 5) govm_kernel(GovmParams p) {
     for (int32_t g = gw; g < total_tiles; g += nw) {
       const int32_t inst = find_instance(sh.tprefix, p.k, g);
       relax_tile<F32>(p, sh.wt[warp], inst, g - sh.tprefix[inst], __ldcg(tails_cur + inst),
-                      sh.tprefix[inst + 1] - sh.tprefix[inst]);
+                      sh.tprefix[inst + 1] - sh.tprefix[inst], p.gsvm ? &ctl->changed[step % 3] : nullptr);
     }
     if (!grid_barrier(ctl, p.wait_limit_ns, &sh.flag)) break;
     // build the next frontier

@@ -26,6 +26,7 @@ DAWN_OK, DAWN_ERR_INVALID, DAWN_ERR_OOM, DAWN_ERR_CUDA = 0, 1, 2, 3
 DAWN_ERR_NOT_CONVERGED, DAWN_ERR_TIMEOUT, DAWN_ERR_BOUNDS = 4, 5, 6
 DAWN_OPT_MAX_STEPS, DAWN_OPT_WAIT_LIMIT_NS, DAWN_OPT_GRID_BLOCKS, DAWN_OPT_TEST_STALL = 1, 2, 3, 4
 DAWN_OPT_TRACE_STEPS = 5
+DAWN_OPT_GSVM = 6
 
 EXPORTS = ("dawn_create_graph", "dawn_set_weights", "dawn_reserve", "dawn_sssp", "dawn_msssp", "dawn_sssp_roots",
            "dawn_sssp_backward", "dawn_status", "dawn_get_stats", "dawn_set_option", "dawn_get_trace", "dawn_graph_info",

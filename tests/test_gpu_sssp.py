@@ -104,6 +104,27 @@ def test_rmat_f32_weights_down_to_zero_exact(dawn):
         assert_exact(rp, cl, w, int(s), d, p, pe)
 
 
+@pytest.mark.parametrize("kind", ["rmat_u32", "grid_f32"])
+def test_gsvm_option_same_result_more_work(dawn, kind):
+    # Algorithm 1 (GSVM) rescans every reached vertex each step; GOVM
+    # (Algorithm 2) only the vertices that changed: same fixpoint, less work
+    wl = gg.rmat_u32(12, 16, nsrc=2, seed=5) if kind == "rmat_u32" else gg.grid_f32(64, 0.01, nsrc=2, seed=5)
+    g = dawn.Graph(wl.row_ptr, wl.col, wl.weights)
+    for s in wl.sources:
+        govm = solve(g, int(s))
+        st_govm = g.stats()
+        g.set_option(dawn.DAWN_OPT_GSVM, 1)
+        gsvm = solve(g, int(s))
+        st_gsvm = g.stats()
+        g.set_option(dawn.DAWN_OPT_GSVM, 0)
+        for a, b in zip(govm, gsvm):
+            assert np.array_equal(a, b)
+        assert_exact(wl.row_ptr, wl.col, wl.weights, int(s), *gsvm)
+        assert st_gsvm["edges_scanned"] > st_govm["edges_scanned"]
+        _, ost = oracle.gsvm(wl.row_ptr, wl.col, wl.weights, int(s))
+        assert st_gsvm["steps"] >= 2 and ost["converged"] == 1
+
+
 def test_unit_weights_bfs_and_mu_one(dawn):
     # Section 4.2: unit weights find every path once (mu = 1)
     wl = gg.rmat_u32(13, 8, nsrc=2, seed=7, wlo=1, whi=1)
