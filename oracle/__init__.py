@@ -34,6 +34,8 @@ _lib = None
 
 U32_INF = np.uint32(0xFFFFFFFF)
 U64_INF = np.uint64(0xFFFFFFFFFFFFFFFF)
+I32_INF = np.int32(0x7FFFFFFF)     # unreachable, signed int32 weights
+I64_INF = np.int64(0x7FFFFFFFFFFFFFFF)
 
 
 class _Stats(ctypes.Structure):
@@ -82,6 +84,14 @@ def _load():
         f.restype = ctypes.c_int
     lib.subtree_grad_f64.argtypes = [i32, vp, i64, vp, vp, vp, vp]
     lib.subtree_grad_f64.restype = ctypes.c_int
+    lib.govm_i32.argtypes = [i32, vp, vp, vp, vp, i32, vp, ctypes.POINTER(_Stats)]
+    lib.govm_i32.restype = ctypes.c_int
+    lib.bellman_ford_i32.argtypes = [i32, vp, vp, vp, vp, i32, vp]
+    lib.bellman_ford_i32.restype = ctypes.c_int
+    lib.parents_i32.argtypes = [i32, vp, vp, vp, vp, i32, vp, vp]
+    lib.parents_i32.restype = ctypes.c_int
+    lib.cert_i32.argtypes = [i32, vp, vp, vp, vp, i32, vp, vp, ctypes.POINTER(i64)]
+    lib.cert_i32.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -98,8 +108,10 @@ def _graph(row_ptr, col, w):
         kind = "u32"
     elif w.dtype == np.float32:
         kind = "f32"
+    elif w.dtype == np.int32:
+        kind = "i32"
     else:
-        raise TypeError("weights must be uint32 or float32")
+        raise TypeError("weights must be uint32, int32 or float32")
     return row_ptr, col, w, kind
 
 
@@ -115,6 +127,31 @@ def _u64_to_u32(d: np.ndarray) -> np.ndarray:
     out = np.full(d.shape, U32_INF, dtype=np.uint32)
     out[fin] = d[fin].astype(np.uint32)
     return out
+
+
+def _i64_to_i32(d: np.ndarray) -> np.ndarray:
+    """int64 exact distances -> int32 with 0x7FFFFFFF for unreachable."""
+    fin = d != I64_INF
+    if np.any(d[fin] >= np.int64(I32_INF)) or np.any(d[fin] < np.int64(-2 ** 31)):
+        raise OverflowError("a shortest distance does not fit in int32")
+    out = np.full(d.shape, I32_INF, dtype=np.int32)
+    out[fin] = d[fin].astype(np.int32)
+    return out
+
+
+def _i32_to_i64(d: np.ndarray) -> np.ndarray:
+    d = _c(d, np.int32)
+    out = d.astype(np.int64)
+    out[d == I32_INF] = I64_INF
+    return out
+
+
+def _dist_in(d, kind):
+    if kind == "u32":
+        return _u32_to_u64(d)
+    if kind == "i32":
+        return _i32_to_i64(d)
+    return _c(d, np.float32)
 
 
 def _u32_to_u64(d: np.ndarray) -> np.ndarray:
@@ -135,7 +172,7 @@ def govm(row_ptr, col, w, roots, algorithm: str = "govm"):
     n = len(row_ptr) - 1
     st = _Stats()
     fn = getattr(lib, f"{algorithm}_{kind}")
-    alpha = np.empty(n, dtype=np.uint64 if kind == "u32" else np.float32)
+    alpha = np.empty(n, dtype={"u32": np.uint64, "i32": np.int64, "f32": np.float32}[kind])
     rc = fn(n, row_ptr.ctypes.data, col.ctypes.data, w.ctypes.data, r.ctypes.data, len(r), alpha.ctypes.data,
             ctypes.byref(st))
     if rc not in (0, 4):
@@ -143,7 +180,7 @@ def govm(row_ptr, col, w, roots, algorithm: str = "govm"):
     stats = {f: getattr(st, f) for f, _ in _Stats._fields_}
     nonroot_reached = max(stats["reached"] - len(np.unique(r)), 0)
     stats["mu"] = stats["updates"] / nonroot_reached if nonroot_reached else 0.0
-    dist = _u64_to_u32(alpha) if kind == "u32" else alpha
+    dist = _u64_to_u32(alpha) if kind == "u32" else (_i64_to_i32(alpha) if kind == "i32" else alpha)
     return dist, stats
 
 
@@ -165,6 +202,25 @@ def dijkstra(row_ptr, col, w, roots):
     return _u64_to_u32(dist) if kind == "u32" else dist
 
 
+def bellman_ford(row_ptr, col, w, roots):
+    """Textbook Bellman-Ford (Section 2.2) for signed int32 weights; returns
+    (dist, negative_cycle_reachable)."""
+    lib = _load()
+    row_ptr, col, w, kind = _graph(row_ptr, col, w)
+    if kind != "i32":
+        raise TypeError("bellman_ford expects int32 weights")
+    r = _roots(roots)
+    n = len(row_ptr) - 1
+    dist = np.empty(n, dtype=np.int64)
+    rc = lib.bellman_ford_i32(n, row_ptr.ctypes.data, col.ctypes.data, w.ctypes.data, r.ctypes.data, len(r),
+                              dist.ctypes.data)
+    if rc < 0:
+        raise MemoryError("bellman_ford failed")
+    if rc == 4:
+        return None, True
+    return _i64_to_i32(dist), False
+
+
 def floyd_warshall(row_ptr, col, w):
     """Dense all-pairs matrix (Section 2.3).  Tiny graphs only."""
     lib = _load()
@@ -182,7 +238,7 @@ def parent_edges(row_ptr, col, w, roots, dist):
     row_ptr, col, w, kind = _graph(row_ptr, col, w)
     r = _roots(roots)
     n = len(row_ptr) - 1
-    d = _u32_to_u64(dist) if kind == "u32" else _c(dist, np.float32)
+    d = _dist_in(dist, kind)
     pe = np.empty(n, dtype=np.int32)
     getattr(lib, f"parents_{kind}")(n, row_ptr.ctypes.data, col.ctypes.data, w.ctypes.data, r.ctypes.data, len(r),
                                     d.ctypes.data, pe.ctypes.data)
@@ -208,7 +264,12 @@ def parent_vertices(row_ptr, roots, dist, parent_edge, kind: str) -> np.ndarray:
 
 def sssp(row_ptr, col, w, roots, algorithm: str = "dijkstra"):
     """(dist, parent, parent_edge) for one solve with the given roots."""
-    if algorithm == "dijkstra":
+    if np.asarray(w).dtype == np.int32:  # signed weights: Dijkstra does not apply
+        dist, neg = bellman_ford(row_ptr, col, w, roots) if algorithm == "dijkstra" else (
+            govm(row_ptr, col, w, roots)[0], False)
+        if neg:
+            raise ValueError("a negative cycle is reachable from the roots")
+    elif algorithm == "dijkstra":
         dist = dijkstra(row_ptr, col, w, roots)
     else:
         dist, _ = govm(row_ptr, col, w, roots, algorithm=algorithm)
@@ -229,7 +290,7 @@ def certificate(row_ptr, col, w, roots, dist, parent_edge):
     row_ptr, col, w, kind = _graph(row_ptr, col, w)
     r = _roots(roots)
     n = len(row_ptr) - 1
-    d = _u32_to_u64(dist) if kind == "u32" else _c(dist, np.float32)
+    d = _dist_in(dist, kind)
     pe = _c(parent_edge, np.int32)
     where = ctypes.c_int64(-1)
     rc = getattr(lib, f"cert_{kind}")(n, row_ptr.ctypes.data, col.ctypes.data, w.ctypes.data, r.ctypes.data,
@@ -280,7 +341,9 @@ def dense_colmin(row_ptr, col, w, source):
 
 def brute_force(row_ptr, col, w, source):
     """min over all simple paths s -> v of the left fold of the edge weights
-    (fl32 for float32, exact for uint32); tiny graphs (n <= 9) only."""
+    (fl32 for float32, exact for integers); tiny graphs (n <= 9) only.  With
+    signed weights this is the shortest distance only when no negative cycle
+    is reachable."""
     row_ptr = [int(x) for x in row_ptr]
     col = [int(x) for x in col]
     w = np.asarray(w)
@@ -302,6 +365,8 @@ def brute_force(row_ptr, col, w, source):
     walk(source, best[source], {source})
     if f32:
         return np.array([np.inf if b is None else b for b in best], dtype=np.float32)
+    if w.dtype == np.int32:
+        return np.array([int(I32_INF) if b is None else b for b in best], dtype=np.int32)
     return np.array([0xFFFFFFFF if b is None else b for b in best], dtype=np.uint32)
 
 

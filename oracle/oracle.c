@@ -605,3 +605,133 @@ int subtree_grad_f64(int32_t n, const int32_t *row_ptr, int64_t m, const int32_t
   free(acc);
   return 0;
 }
+
+/* ======================================================== signed weights */
+
+/*
+ * Signed integer weights (Section 1 contribution 4: the weighted DAWN
+ * handles negative weights).  Distances are exact int64 values; I64_INF marks
+ * unreachable vertices.  Algorithm 2 is run as written with the step cap n
+ * as the only guard: a run that is still changing after n steps (a negative
+ * cycle reachable from a root) reports "not converged".
+ */
+#define I64_INF INT64_MAX
+
+int govm_i32(int32_t n, const int32_t *row_ptr, const int32_t *col, const int32_t *w, const int32_t *roots,
+             int32_t k, int64_t *alpha, or_stats *st) {
+  uint8_t *is_root = mark_roots(n, roots, k);
+  uint8_t *delta = (uint8_t *)calloc((size_t)n, 1);
+  uint8_t *beta = (uint8_t *)calloc((size_t)n, 1);
+  int32_t *count = (int32_t *)calloc((size_t)n, sizeof(int32_t));
+  if (!is_root || !delta || !beta || !count) { free(is_root); free(delta); free(beta); free(count); return -1; }
+  memset(st, 0, sizeof(*st));
+  for (int32_t v = 0; v < n; ++v) alpha[v] = I64_INF;
+  for (int32_t i = 0; i < k; ++i) { alpha[roots[i]] = 0; delta[roots[i]] = 1; }
+  int64_t step = 0;
+  while (step < n) {
+    step = step + 1;
+    int ptr = 0;
+    for (int32_t j = 0; j < n; ++j) {
+      int32_t start = row_ptr[j], end = row_ptr[j + 1];
+      if (delta[j] && start != end) {
+        st->frontier_sum++;
+        for (int32_t e = start; e < end; ++e) {
+          int32_t index = col[e];
+          int64_t value = w[e];
+          st->edges_scanned++;
+          if (alpha[index] > alpha[j] + value && !is_root[index]) {
+            alpha[index] = alpha[j] + value;
+            beta[index] = 1;
+            count[index]++;
+            st->updates++;
+            ptr = 1;
+          }
+        }
+      }
+    }
+    if (!ptr) { st->converged = 1; break; }
+    memcpy(delta, beta, (size_t)n);
+    memset(beta, 0, (size_t)n);
+  }
+  st->steps = step;
+  uint8_t *finite = delta;
+  for (int32_t v = 0; v < n; ++v) finite[v] = alpha[v] != I64_INF;
+  finish_stats(st, n, finite, count);
+  free(is_root); free(delta); free(beta); free(count);
+  return st->converged ? 0 : 4;
+}
+
+/* Textbook Bellman-Ford: n - 1 rounds over every edge, then one more round
+ * that detects a reachable negative cycle (returns 4). */
+int bellman_ford_i32(int32_t n, const int32_t *row_ptr, const int32_t *col, const int32_t *w, const int32_t *roots,
+                     int32_t k, int64_t *dist) {
+  uint8_t *is_root = mark_roots(n, roots, k);
+  if (!is_root) return -1;
+  for (int32_t v = 0; v < n; ++v) dist[v] = I64_INF;
+  for (int32_t i = 0; i < k; ++i) dist[roots[i]] = 0;
+  for (int32_t round = 0; round < n - 1; ++round) {
+    int changed = 0;
+    for (int32_t u = 0; u < n; ++u) {
+      if (dist[u] == I64_INF) continue;
+      for (int32_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e) {
+        int32_t v = col[e];
+        if (!is_root[v] && dist[u] + w[e] < dist[v]) { dist[v] = dist[u] + w[e]; changed = 1; }
+      }
+    }
+    if (!changed) break;
+  }
+  int rc = 0;
+  for (int32_t u = 0; u < n && !rc; ++u) {
+    if (dist[u] == I64_INF) continue;
+    for (int32_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e)
+      if (!is_root[col[e]] && dist[u] + w[e] < dist[col[e]]) { rc = 4; break; }
+  }
+  free(is_root);
+  return rc;
+}
+
+int parents_i32(int32_t n, const int32_t *row_ptr, const int32_t *col, const int32_t *w, const int32_t *roots,
+                int32_t k, const int64_t *dist, int32_t *parent_edge) {
+  uint8_t *is_root = mark_roots(n, roots, k);
+  if (!is_root) return -1;
+  for (int32_t v = 0; v < n; ++v) parent_edge[v] = -1;
+  for (int32_t u = 0; u < n; ++u) {
+    if (dist[u] == I64_INF) continue;
+    for (int32_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e) {
+      int32_t v = col[e];
+      if (is_root[v] || parent_edge[v] != -1) continue;
+      if (dist[u] + w[e] == dist[v]) parent_edge[v] = e;
+    }
+  }
+  free(is_root);
+  return 0;
+}
+
+int cert_i32(int32_t n, const int32_t *row_ptr, const int32_t *col, const int32_t *w, const int32_t *roots,
+             int32_t k, const int64_t *dist, const int32_t *parent_edge, int64_t *where) {
+  int64_t m = row_ptr[n];
+  uint8_t *is_root = mark_roots(n, roots, k);
+  uint8_t *finite = (uint8_t *)calloc((size_t)n, 1);
+  if (!is_root || !finite) { free(is_root); free(finite); return -1; }
+  int rc = 0;
+  for (int32_t v = 0; v < n; ++v) finite[v] = dist[v] != I64_INF;
+  for (int32_t v = 0; v < n && !rc; ++v)
+    if (is_root[v] && (dist[v] != 0 || parent_edge[v] != -1)) { rc = 1; *where = v; }
+  for (int32_t u = 0; u < n && !rc; ++u) {
+    if (!finite[u]) continue;
+    for (int32_t e = row_ptr[u]; e < row_ptr[u + 1]; ++e)
+      if (!is_root[col[e]] && dist[u] + w[e] < dist[col[e]]) { rc = 2; *where = e; break; }
+  }
+  for (int32_t v = 0; v < n && !rc; ++v) {
+    if (is_root[v]) continue;
+    int32_t e = parent_edge[v];
+    if (!finite[v]) { if (e != -1) { rc = 4; *where = v; } continue; }
+    if (e < 0 || e >= m || col[e] != v) { rc = 3; *where = v; break; }
+    int32_t lo = 0, hi = n;
+    while (hi - lo > 1) { int32_t mid = lo + (hi - lo) / 2; if (row_ptr[mid] <= e) lo = mid; else hi = mid; }
+    if (!finite[lo] || dist[lo] + w[e] != dist[v]) { rc = 3; *where = v; }
+  }
+  if (!rc) rc = cert_tree(n, row_ptr, col, is_root, finite, parent_edge, where);
+  free(is_root); free(finite);
+  return rc;
+}

@@ -395,3 +395,79 @@ def test_generators_shapes():
     rp, cl, sc = gg.grid(16, 0.01, 0)
     assert len(cl) == 4 * 16 * 15 + int(0.01 * 4 * 16 * 15)
     assert gg.tiny_er().weights.tobytes() == wl.weights.tobytes()  # deterministic
+
+
+# ------------------------------------------------------------ signed weights
+
+def potential_reweighted(n, m, seed, pmax=50):
+    """Random graph with non-negative u32 weights w and potentials p; the
+    reweighted int32 weights w + p[u] - p[v] are often negative but create no
+    negative cycle (every cycle keeps its original, non-negative length)."""
+    rp, cl, w = gg.random_small(n, m, seed, kind="u32", wlo=0, whi=30, self_loops=True)
+    p = gg.below(seed, 21, n, 2 * pmax + 1) - pmax
+    tails = oracle.edge_tails(rp)
+    w2 = (w.astype(np.int64) + p[tails] - p[cl]).astype(np.int32)
+    return rp, cl, w, w2, p
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_signed_weights_potential_closed_form(seed):
+    # path lengths under w + p[u] - p[v] telescope: dist'(v) = dist(v) + p[s] - p[v];
+    # the tight (parent) edges are the same set
+    rp, cl, w, w2, p = potential_reweighted(150, 900, seed)
+    assert (w2 < 0).any()
+    s = 3
+    d = oracle.dijkstra(rp, cl, w, s)
+    fin = d != INF32
+    expect = d.astype(np.int64)[fin] + p[s] - p[np.nonzero(fin)[0]]
+    for algo in ("govm", "bellman_ford"):
+        if algo == "govm":
+            d2, st = oracle.govm(rp, cl, w2, s)
+            assert st["converged"] == 1
+        else:
+            d2, neg = oracle.bellman_ford(rp, cl, w2, s)
+            assert not neg
+        assert np.array_equal(d2 == oracle.I32_INF, ~fin)
+        assert np.array_equal(d2[fin].astype(np.int64), expect)
+    pe = oracle.parent_edges(rp, cl, w, s, d)
+    pe2 = oracle.parent_edges(rp, cl, w2, s, d2)
+    assert np.array_equal(pe, pe2)
+    assert oracle.certificate(rp, cl, w2, s, d2, pe2)[0] == 0
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_signed_weights_against_scipy_bellman_ford(seed):
+    rp, cl, w, w2, p = potential_reweighted(200, 1200, seed + 10)
+    n = len(rp) - 1
+    tails = oracle.edge_tails(rp)
+    best = {}
+    for u, v, x in zip(tails, cl, w2.astype(np.float64)):
+        if u == v:
+            continue
+        if (u, v) not in best or x < best[(u, v)]:
+            best[(u, v)] = x
+    uu, vv = zip(*best.keys())
+    A = sp.csr_matrix((list(best.values()), (uu, vv)), shape=(n, n))
+    ref = scipy_csgraph.bellman_ford(A, directed=True, indices=0)
+    d2 = oracle.govm(rp, cl, w2, 0)[0]
+    got = d2.astype(np.float64)
+    got[d2 == oracle.I32_INF] = np.inf
+    assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_signed_weights_brute_force_small(seed):
+    rp, cl, w, w2, p = potential_reweighted(7, 16, seed + 30, pmax=9)
+    assert np.array_equal(oracle.govm(rp, cl, w2, 0)[0], oracle.brute_force(rp, cl, w2, 0))
+
+
+def test_negative_cycle_reported():
+    # 0 -> 1 -> 2 -> 1 with w(1,2) + w(2,1) = -1: reachable negative cycle
+    rp, cl, w = gg.csr_from_edges(4, [(0, 1), (1, 2), (2, 1), (2, 3)], np.array([4, 2, -3, 1], np.int32), np.int32)
+    d, st = oracle.govm(rp, cl, w, 0)
+    assert st["converged"] == 0 and st["steps"] == 4  # the step cap n of Algorithm 2
+    assert oracle.bellman_ford(rp, cl, w, 0)[1] is True
+    # a negative cycle that is not reachable does not matter
+    assert oracle.bellman_ford(rp, cl, w, 3)[1] is False
+    d3, st3 = oracle.govm(rp, cl, w, 3)
+    assert st3["converged"] == 1 and d3.tolist() == [int(oracle.I32_INF)] * 3 + [0]
