@@ -26,7 +26,13 @@
  *  - Distances: uint32 graphs report uint32 distances with 0xFFFFFFFF for
  *    unreachable vertices; float32 graphs report float32 distances, each the
  *    round-to-nearest left fold fl(...fl(0 + w1) + ... + wk) along a shortest
- *    path, with +inf for unreachable vertices.
+ *    path, with +inf for unreachable vertices; int32 graphs (signed weights,
+ *    Section 1 contribution 4) report int32 distances with 0x7FFFFFFF
+ *    (INT32_MAX) for unreachable vertices.
+ *  - Negative weights (int32 graphs): the iteration is capped at n steps as
+ *    in Algorithm 2 ("while step < n"); without a negative cycle reachable
+ *    from a source it converges before the cap, with one the solve reports
+ *    DAWN_ERR_NOT_CONVERGED and its outputs are the state after n steps.
  *  - Parents: parent[v] is the tail u of the lowest-index CSR edge e = (u->v)
  *    with fl(dist[u] + w[e]) == dist[v]; parent[source] = source;
  *    parent[unreachable] = -1.  parent_edge[v] is that edge index e, or -1
@@ -47,7 +53,7 @@ extern "C" {
 
 typedef struct dawn_graph_s *dawn_graph; /* opaque, owned by the library */
 
-typedef enum { DAWN_W_U32 = 0, DAWN_W_F32 = 1 } dawn_wtype;
+typedef enum { DAWN_W_U32 = 0, DAWN_W_F32 = 1, DAWN_W_I32 = 2 } dawn_wtype;
 
 typedef enum {
   DAWN_OK = 0,
@@ -78,10 +84,12 @@ typedef struct {
  *   row_ptr      int32[n+1], row_ptr[0] = 0, non-decreasing, row_ptr[n] = m
  *   col_idx      int32[m], every entry in [0, n); parallel edges and
  *                self-loops are allowed
- *   weights      uint32[m] (wtype DAWN_W_U32) or float32[m] (DAWN_W_F32);
- *                float weights must be finite and >= 0; uint32 weights must
- *                satisfy n * max(w) < 0xFFFFFFFF so that no path sum can
- *                reach the unreachable sentinel
+ *   weights      uint32[m] (wtype DAWN_W_U32), float32[m] (DAWN_W_F32) or
+ *                int32[m] (DAWN_W_I32, may be negative); float weights must
+ *                be finite and >= 0; uint32 weights must satisfy
+ *                n * max(w) < 0xFFFFFFFF and int32 weights
+ *                n * max|w| < 0x7FFFFFFF, so that no path sum can reach the
+ *                unreachable sentinel
  *   inputs_on_device  0: the three arrays are host memory; 1: device memory
  *   stream       stream for the copies and the validation kernel
  *   out          receives the handle

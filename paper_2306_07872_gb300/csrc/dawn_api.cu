@@ -53,7 +53,7 @@ namespace {
 enum : unsigned { kBadRowPtr = 1u, kBadCol = 2u, kBadWeight = 4u };
 
 __global__ void validate_kernel(const int32_t *row_ptr, const int32_t *col, const uint32_t *w, int32_t n, int64_t m,
-                                int is_f32, unsigned *flags) {
+                                int wtype, unsigned *flags) {
   const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long gsize = (long long)gridDim.x * blockDim.x;
   unsigned bad = 0, wmax = 0;
@@ -69,9 +69,12 @@ __global__ void validate_kernel(const int32_t *row_ptr, const int32_t *col, cons
       if (c < 0 || c >= n) bad |= kBadCol;
     }
     const uint32_t x = w[e];
-    if (is_f32) {
+    if (wtype == DAWN_W_F32) {
       const float f = __uint_as_float(x);
       if (!(f >= 0.0f) || isinf(f)) bad |= kBadWeight;  // NaN fails f >= 0
+    } else if (wtype == DAWN_W_I32) {
+      const int32_t y = (int32_t)x;
+      wmax = max(wmax, y < 0 ? (uint32_t)(-(int64_t)y) : (uint32_t)y);  // |w|
     } else {
       wmax = max(wmax, x);
     }
@@ -207,7 +210,7 @@ int ensure_workspace(dawn_graph g, int32_t k) {
 }
 
 int grid_for(dawn_graph g, int32_t k) {
-  if (g->blocks_per_sm == 0) g->blocks_per_sm = std::max(1, dawn::govm_max_blocks_per_sm(g->wtype == DAWN_W_F32));
+  if (g->blocks_per_sm == 0) g->blocks_per_sm = std::max(1, dawn::govm_max_blocks_per_sm(g->wtype));
   const int per_sm = g->blocks_per_sm;
   const int cap = per_sm * g->sms;
   if (g->grid_blocks > 0) return std::min(g->grid_blocks, cap);
@@ -253,7 +256,7 @@ int run_solve(dawn_graph g, const int32_t *seeds, int32_t nseeds, int32_t source
   if (e == cudaSuccess && g->trace)
     e = cudaMemsetAsync(g->trace, 0, (size_t)g->trace_cap * 4 * sizeof(unsigned long long), stream);
   if (e != cudaSuccess) return cuda_fail(e);
-  e = dawn::launch_govm(p, g->wtype == DAWN_W_F32, grid_for(g, k), stream);
+  e = dawn::launch_govm(p, g->wtype, grid_for(g, k), stream);
   if (e != cudaSuccess) return cuda_fail(e);
   g->last_stream = stream;
   return DAWN_OK;
@@ -276,7 +279,7 @@ int validate(dawn_graph g, cudaStream_t stream) {
   if (e != cudaSuccess) return cuda_fail(e);
   const int64_t work = std::max<int64_t>(g->m, (int64_t)g->n + 1);
   const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((work + 255) / 256, (int64_t)g->sms * 8));
-  validate_kernel<<<blocks, 256, 0, stream>>>(g->row_ptr, g->col, g->w, g->n, g->m, g->wtype == DAWN_W_F32,
+  validate_kernel<<<blocks, 256, 0, stream>>>(g->row_ptr, g->col, g->w, g->n, g->m, g->wtype,
                                                g->vflags);
   unsigned h[2] = {0, 0};
   e = cudaGetLastError();
@@ -287,6 +290,9 @@ int validate(dawn_graph g, cudaStream_t stream) {
   // uint32: every candidate dist(u) + w is at most n * max(w) (shortest paths
   // are simple); it must stay below the unreachable sentinel.
   if (g->wtype == DAWN_W_U32 && (uint64_t)g->n * (uint64_t)h[1] >= 0xFFFFFFFFull) return DAWN_ERR_INVALID;
+  // int32: every simple-path sum and candidate lies in [-n max|w|, n max|w|],
+  // which must stay inside int32 and below the unreachable sentinel INT32_MAX
+  if (g->wtype == DAWN_W_I32 && (uint64_t)g->n * (uint64_t)h[1] >= 0x7FFFFFFFull) return DAWN_ERR_INVALID;
   return DAWN_OK;
 }
 
@@ -325,7 +331,7 @@ int dawn_create_graph(int32_t n, int64_t m, const int32_t *row_ptr, const int32_
   if (!out) return DAWN_ERR_INVALID;
   *out = nullptr;
   if (n < 1 || m < 0 || m > 0x7FFFFFFF || !row_ptr || (m > 0 && (!col_idx || !weights)) ||
-      (wtype != DAWN_W_U32 && wtype != DAWN_W_F32))
+      (wtype != DAWN_W_U32 && wtype != DAWN_W_F32 && wtype != DAWN_W_I32))
     return DAWN_ERR_INVALID;
   dawn_graph g = new (std::nothrow) dawn_graph_s();
   if (!g) return DAWN_ERR_OOM;
@@ -623,7 +629,7 @@ extern "C" int dawn_sssp_noalloc(dawn_graph g, int32_t source, void *dist, int32
   // the control block (barrier counters, status) must start at zero; the
   // kernel itself resets everything else it reads
   cudaError_t e = cudaMemsetAsync(ctl, 0, sizeof(DeviceCtl), s);
-  if (e == cudaSuccess) e = dawn::launch_govm(p, g->wtype == DAWN_W_F32, grid_for(g, 1), s);
+  if (e == cudaSuccess) e = dawn::launch_govm(p, g->wtype, grid_for(g, 1), s);
   if (e == cudaSuccess && status_out)
     e = cudaMemcpyAsync(status_out, &ctl->status, sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
   if (e != cudaSuccess) return cuda_fail(e);

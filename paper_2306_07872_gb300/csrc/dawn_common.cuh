@@ -3,9 +3,10 @@
 // Data layout in device memory (one solver workspace per graph handle, k
 // instances):
 //   state   u64 [k][n]   alpha, packed (key(dist) << 32) | parent edge.
-//                        key(d) is d itself for uint32 weights and the IEEE
-//                        bit pattern for non-negative float32 weights; both
-//                        are monotone in d, so one 64-bit atomicMin updates
+//                        key(d) is d itself for uint32 weights, the IEEE
+//                        bit pattern for non-negative float32 weights and the
+//                        offset-binary code for signed int32; all are monotone
+//                        in d, so one 64-bit atomicMin updates
 //                        distance and parent edge together and keeps the
 //                        lexicographically smallest (dist, edge) pair.
 //   bitmap  u32 [k][words]   beta of Algorithm 2: vertices whose distance
@@ -83,7 +84,7 @@ struct GovmParams {
 };
 
 // Host-side launchers (govm_kernel.cu).
-cudaError_t launch_govm(const GovmParams &p, int is_f32, int grid_blocks, cudaStream_t stream);
-int govm_max_blocks_per_sm(int is_f32);
+cudaError_t launch_govm(const GovmParams &p, int wtype, int grid_blocks, cudaStream_t stream);
+int govm_max_blocks_per_sm(int wtype);
 
 }  // namespace dawn

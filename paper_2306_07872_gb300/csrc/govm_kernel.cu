@@ -64,21 +64,38 @@ __device__ __forceinline__ unsigned long long global_ns() {
   return t;
 }
 
-// Distance keys: uint32 distances are their own key; non-negative float32
-// distances are keyed by their bit pattern (monotone for x >= 0).
-template <bool F32>
+// Distance keys, monotone in the distance so that the packed atomicMin
+// orders by distance: uint32 distances are their own key; non-negative
+// float32 distances are keyed by their bit pattern; signed int32 distances
+// by their offset-binary code (sign bit flipped).  `zero` is the key of a
+// source, `inf` of an unreachable vertex; `out` turns a key back into the
+// bits of the output distance.
+template <int WT>
 struct Key;
 template <>
-struct Key<false> {
+struct Key<DAWN_W_U32> {
   static constexpr uint32_t inf = kInfKeyU32;
+  static constexpr uint32_t zero = 0u;
   static __device__ __forceinline__ uint32_t add(uint32_t d, uint32_t w) { return d + w; }
+  static __device__ __forceinline__ uint32_t out(uint32_t k) { return k; }
 };
 template <>
-struct Key<true> {
+struct Key<DAWN_W_F32> {
   static constexpr uint32_t inf = kInfKeyF32;
+  static constexpr uint32_t zero = 0u;
   static __device__ __forceinline__ uint32_t add(uint32_t d, uint32_t w) {
     return __float_as_uint(__fadd_rn(__uint_as_float(d), __uint_as_float(w)));
   }
+  static __device__ __forceinline__ uint32_t out(uint32_t k) { return k; }
+};
+template <>
+struct Key<DAWN_W_I32> {
+  static constexpr uint32_t inf = 0xFFFFFFFFu;   // INT32_MAX: unreachable
+  static constexpr uint32_t zero = 0x80000000u;  // distance 0
+  static __device__ __forceinline__ uint32_t add(uint32_t d, uint32_t w) {
+    return (uint32_t)((int32_t)(d ^ 0x80000000u) + (int32_t)w) ^ 0x80000000u;
+  }
+  static __device__ __forceinline__ uint32_t out(uint32_t k) { return k ^ 0x80000000u; }
 };
 
 struct WarpTile {
@@ -340,7 +357,7 @@ __device__ void build_frontier(const GovmParams &p, unsigned long long *tails_ne
 }
 
 // Relax the out-edges in virtual-edge tile t of instance inst's frontier.
-template <bool F32>
+template <int WT>
 __device__ __forceinline__ void relax_tile(const GovmParams &p, WarpTile &wt, int32_t inst, int32_t t,
                                            unsigned long long tail_cur, int32_t tiles_i, unsigned *changed) {
   const int lane = threadIdx.x & 31;
@@ -352,7 +369,7 @@ __device__ __forceinline__ void relax_tile(const GovmParams &p, WarpTile &wt, in
   const uint4 *q = p.queue + (size_t)inst * p.n;
   uint32_t *bm = p.bitmap + (size_t)inst * p.words;
   unsigned long long *st = p.state + (size_t)inst * p.n;
-  const unsigned long long kSourceState = (unsigned long long)kNoEdge;  // key 0, no parent edge
+  const unsigned long long kSourceState = ((unsigned long long)Key<WT>::zero << 32) | kNoEdge;  // no parent edge
 
   __syncwarp();  // the previous tile of this warp has finished with wt
   const int32_t ia = __ldcg(tiles + t);
@@ -437,7 +454,7 @@ __device__ __forceinline__ void relax_tile(const GovmParams &p, WarpTile &wt, in
   unsigned need = 0;
 #pragma unroll
   for (int r = 0; r < kEdgesPerLane; ++r) {
-    ckey[r] = Key<F32>::add(wt.dkey[wt.own[r * 32 + lane]], cw[r].y);
+    ckey[r] = Key<WT>::add(wt.dkey[wt.own[r * 32 + lane]], cw[r].y);
     const unsigned long long cand = ((unsigned long long)ckey[r] << 32) | eidx[r];
     if ((valid & (1u << r)) && cand < curst[r] && curst[r] != kSourceState) need |= 1u << r;
   }
@@ -458,7 +475,7 @@ __device__ __forceinline__ void relax_tile(const GovmParams &p, WarpTile &wt, in
   if (changed && __any_sync(kFull, strict != 0) && lane == 0) atomicOr(changed, 1u);
 }
 
-template <bool F32>
+template <int WT>
 __global__ void __launch_bounds__(kBlockThreads, 5) govm_kernel(GovmParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   BlockShared &sh = *reinterpret_cast<BlockShared *>(smem_raw);
@@ -466,8 +483,8 @@ __global__ void __launch_bounds__(kBlockThreads, 5) govm_kernel(GovmParams p) {
   const long long gtid = (long long)blockIdx.x * blockDim.x + tid;
   const long long gsize = (long long)gridDim.x * blockDim.x;
   DeviceCtl *ctl = p.ctl;
-  const unsigned long long kInfState = ((unsigned long long)Key<F32>::inf << 32) | kNoEdge;
-  const unsigned long long kSourceState = (unsigned long long)kNoEdge;
+  const unsigned long long kInfState = ((unsigned long long)Key<WT>::inf << 32) | kNoEdge;
+  const unsigned long long kSourceState = ((unsigned long long)Key<WT>::zero << 32) | kNoEdge;
   unsigned long long updates = 0;  // vertices entering beta, summed over steps
   unsigned long long seeded = 0;   // the seeds' own marks (not path updates)
   long long step = 0;
@@ -555,7 +572,7 @@ __global__ void __launch_bounds__(kBlockThreads, 5) govm_kernel(GovmParams p) {
     const int32_t nw = gridDim.x * kWarpsPerBlock;
     for (int32_t g = gw; g < total_tiles; g += nw) {
       const int32_t inst = find_instance(sh.tprefix, p.k, g);
-      relax_tile<F32>(p, sh.wt[warp], inst, g - sh.tprefix[inst], __ldcg(tails_cur + inst),
+      relax_tile<WT>(p, sh.wt[warp], inst, g - sh.tprefix[inst], __ldcg(tails_cur + inst),
                       sh.tprefix[inst + 1] - sh.tprefix[inst], p.gsvm ? &ctl->changed[step % 3] : nullptr);
     }
     if (!grid_barrier(ctl, p.wait_limit_ns, &sh.flag)) break;
@@ -584,8 +601,8 @@ __global__ void __launch_bounds__(kBlockThreads, 5) govm_kernel(GovmParams p) {
         const unsigned long long s = __ldcg(st + v);
         const uint32_t key = (uint32_t)(s >> 32);
         const uint32_t e = (uint32_t)s;
-        const bool unreachable = key == Key<F32>::inf;
-        dist[v] = key;
+        const bool unreachable = key == Key<WT>::inf;
+        dist[v] = Key<WT>::out(key);
         if (par) par[v] = unreachable ? -1 : (e == kNoEdge ? (int32_t)v : __ldg(p.src + e));
         if (pe) pe[v] = (unreachable || e == kNoEdge) ? -1 : (int32_t)e;
       }
@@ -607,17 +624,21 @@ finish:
 cudaError_t prepare_kernels() {
   static bool done = false;
   if (done) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(govm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(govm_kernel<DAWN_W_U32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)sizeof(BlockShared));
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(govm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(BlockShared));
+    e = cudaFuncSetAttribute(govm_kernel<DAWN_W_F32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(BlockShared));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(govm_kernel<DAWN_W_I32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(BlockShared));
   done = e == cudaSuccess;
   return e;
 }
 
 }  // namespace
 
-cudaError_t launch_govm(const GovmParams &p, int is_f32, int grid_blocks, cudaStream_t stream) {
+cudaError_t launch_govm(const GovmParams &p, int wtype, int grid_blocks, cudaStream_t stream) {
   cudaError_t e = prepare_kernels();
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
@@ -630,16 +651,19 @@ cudaError_t launch_govm(const GovmParams &p, int is_f32, int grid_blocks, cudaSt
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  if (is_f32) return cudaLaunchKernelEx(&cfg, govm_kernel<true>, p);
-  return cudaLaunchKernelEx(&cfg, govm_kernel<false>, p);
+  if (wtype == DAWN_W_F32) return cudaLaunchKernelEx(&cfg, govm_kernel<DAWN_W_F32>, p);
+  if (wtype == DAWN_W_I32) return cudaLaunchKernelEx(&cfg, govm_kernel<DAWN_W_I32>, p);
+  return cudaLaunchKernelEx(&cfg, govm_kernel<DAWN_W_U32>, p);
 }
 
-int govm_max_blocks_per_sm(int is_f32) {
+int govm_max_blocks_per_sm(int wtype) {
   int nb = 0;
   if (prepare_kernels() != cudaSuccess) return 0;
   const size_t smem = sizeof(BlockShared);
-  cudaError_t e = is_f32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, govm_kernel<true>, kBlockThreads, smem)
-                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, govm_kernel<false>, kBlockThreads, smem);
+  cudaError_t e =
+      wtype == DAWN_W_F32   ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, govm_kernel<DAWN_W_F32>, kBlockThreads, smem)
+      : wtype == DAWN_W_I32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, govm_kernel<DAWN_W_I32>, kBlockThreads, smem)
+                            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, govm_kernel<DAWN_W_U32>, kBlockThreads, smem);
   return e == cudaSuccess ? nb : 0;
 }
 

@@ -21,7 +21,7 @@ import torch
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libdawn.so")
 
-DAWN_W_U32, DAWN_W_F32 = 0, 1
+DAWN_W_U32, DAWN_W_F32, DAWN_W_I32 = 0, 1, 2
 DAWN_OK, DAWN_ERR_INVALID, DAWN_ERR_OOM, DAWN_ERR_CUDA = 0, 1, 2, 3
 DAWN_ERR_NOT_CONVERGED, DAWN_ERR_TIMEOUT, DAWN_ERR_BOUNDS = 4, 5, 6
 DAWN_OPT_MAX_STEPS, DAWN_OPT_WAIT_LIMIT_NS, DAWN_OPT_GRID_BLOCKS, DAWN_OPT_TEST_STALL = 1, 2, 3, 4
@@ -125,8 +125,10 @@ def dawn_create_graph(row_ptr: torch.Tensor, col_idx: torch.Tensor, weights: tor
         wt = DAWN_W_U32
     elif weights.dtype == torch.float32:
         wt = DAWN_W_F32
+    elif weights.dtype == torch.int32:
+        wt = DAWN_W_I32
     else:
-        raise TypeError("weights must be torch.uint32 or torch.float32")
+        raise TypeError("weights must be torch.uint32, torch.int32 or torch.float32")
     rp, on_dev = _any(row_ptr, torch.int32, "row_ptr")
     cl, d2 = _any(col_idx, torch.int32, "col_idx")
     w, d3 = _any(weights, weights.dtype, "weights")
@@ -244,7 +246,7 @@ class Graph:
         with torch.cuda.device(self.device):
             self.handle = dawn_create_graph(row_ptr, col_idx, weights, stream)
         self.n, self.m, self.wtype = dawn_graph_info(self.handle)
-        self.dist_dtype = torch.uint32 if self.wtype == DAWN_W_U32 else torch.float32
+        self.dist_dtype = {DAWN_W_U32: torch.uint32, DAWN_W_F32: torch.float32, DAWN_W_I32: torch.int32}[self.wtype]
 
     def close(self):
         if getattr(self, "handle", None):

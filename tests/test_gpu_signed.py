@@ -1,0 +1,80 @@
+"""GPU parity with signed int32 weights (negative weights, Section 1
+contribution 4): graphs without negative cycles come from non-negative
+graphs reweighted by vertex potentials; distances must equal the oracle's
+Bellman-Ford exactly and parents its lowest-index rule; a reachable negative
+cycle makes the solve stop at the step cap with DAWN_ERR_NOT_CONVERGED."""
+import numpy as np
+import pytest
+import torch
+
+import graphgen as gg
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dawn():
+    import paper_2306_07872_gb300 as pkg
+    pkg.load_library()
+    return pkg
+
+
+def reweight(rp, cl, w, seed, pmax):
+    p = gg.below(seed, 21, len(rp) - 1, 2 * pmax + 1) - pmax
+    tails = oracle.edge_tails(rp)
+    return (w.astype(np.int64) + p[tails] - p[cl]).astype(np.int32)
+
+
+def check(dawn, rp, cl, w2, sources):
+    g = dawn.Graph(rp, cl, w2)
+    for s in sources:
+        d, p, pe = g.sssp(int(s), parent=True, parent_edge=True)
+        d_ref, p_ref, pe_ref = oracle.sssp(rp, cl, w2, int(s))
+        assert np.array_equal(d.cpu().numpy(), d_ref)
+        assert np.array_equal(pe.cpu().numpy(), pe_ref) and np.array_equal(p.cpu().numpy(), p_ref)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_signed_random_exact(dawn, seed):
+    rp, cl, w = gg.random_small(400, 3000, seed, kind="u32", wlo=0, whi=40, self_loops=True)
+    w2 = reweight(rp, cl, w, seed, 60)
+    assert (w2 < 0).any()
+    check(dawn, rp, cl, w2, (0, 7, 123))
+
+
+def test_signed_rmat_exact(dawn):
+    wl = gg.rmat_u32(13, 16, nsrc=3, seed=6, wlo=1, whi=255)
+    w2 = reweight(wl.row_ptr, wl.col, wl.weights, 6, 200)
+    check(dawn, wl.row_ptr, wl.col, w2, wl.sources)
+
+
+def test_signed_msssp_exact(dawn):
+    rp, cl, w = gg.random_small(300, 2000, 9, kind="u32", wlo=0, whi=20)
+    w2 = reweight(rp, cl, w, 9, 30)
+    g = dawn.Graph(rp, cl, w2)
+    src = np.arange(0, 300, 7, dtype=np.int32)
+    dist, _ = g.msssp(src, parent=False)
+    dist = dist.cpu().numpy()
+    for i, s in enumerate(src):
+        assert np.array_equal(dist[i], oracle.bellman_ford(rp, cl, w2, int(s))[0])
+
+
+def test_negative_cycle_not_converged(dawn):
+    rp, cl, w = gg.csr_from_edges(4, [(0, 1), (1, 2), (2, 1), (2, 3)], np.array([4, 2, -3, 1], np.int32), np.int32)
+    g = dawn.Graph(rp, cl, w)
+    with pytest.raises(dawn.DawnError) as e:
+        g.sssp(0)
+    assert e.value.code == dawn.DAWN_ERR_NOT_CONVERGED
+    d, _, _ = g.sssp(3)  # the cycle is not reachable from vertex 3
+    assert d.cpu().tolist() == [0x7FFFFFFF] * 3 + [0]
+
+
+def test_signed_overflow_bound_rejected(dawn):
+    rp = np.array([0, 1, 2], np.int32)
+    with pytest.raises(dawn.DawnError) as e:  # 2 * 2^30 reaches INT32_MAX
+        dawn.Graph(rp, np.array([1, 0], np.int32), np.array([-(1 << 30), 5], np.int32))
+    assert e.value.code == dawn.DAWN_ERR_INVALID
+    g = dawn.Graph(rp, np.array([1, 0], np.int32), np.array([-(1 << 29), 5], np.int32))
+    with pytest.raises(dawn.DawnError):  # 0 -> 1 -> 0 is a negative cycle
+        g.sssp(0)
