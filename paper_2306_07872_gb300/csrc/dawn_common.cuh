@@ -14,7 +14,10 @@
 //   queue   uint4[k][n]  delta of Algorithm 2, compacted: one entry per
 //                        frontier vertex with an out-edge = (row start,
 //                        offset of its first edge in the frontier's virtual
-//                        edge list, distance key, vertex id).
+//                        edge list, row start minus that offset (mod 2^32),
+//                        vertex id).  No distance is stored: the relax phase
+//                        reads the vertex's current key, which is never
+//                        above the key it had when the entry was built.
 //   tiles   i32 [k][tiles_cap]  entry index owning the first virtual edge of
 //                        every kTile-edge tile of the frontier.
 //   tails   u64 [2][k]   per-instance frontier size (low 32 bits) and total
@@ -42,8 +45,7 @@ constexpr uint32_t kInfKeyF32 = 0x7F800000u;  // +inf
 
 // Control block: barrier, status and counters (zeroed before every launch).
 struct DeviceCtl {
-  unsigned int bar_count;
-  unsigned int bar_gen;
+  unsigned long long bar;  // device-wide barrier: arrivals (bits 0-62), error flag (bit 63)
   int status;
   int stall_flag;  // never set by anyone: the test stall waits on it
   unsigned long long steps;

@@ -13,10 +13,10 @@
 //              together) and marks beta for every candidate that beats the
 //              distance it read; both are fire-and-forget reductions, so no
 //              warp waits for an atomic's result;
-//      build   beta is consumed word by word and compacted into delta (one
-//              entry per marked vertex with an out-edge, ordered by vertex
-//              id), one block-aggregated atomicAdd per 256 words reserving
-//              entries and edge offsets together;
+//      build   beta is consumed in 32-word chunks and compacted into delta
+//              (one entry per marked vertex with an out-edge), one warp
+//              atomicAdd per 128 vertices reserving entries and edge offsets
+//              together;
 //      each phase ends with a device-wide barrier (bounded wait); the loop
 //      stops when delta is empty (no path changed) or at the step cap;
 //   4. unpack dist / parent / parent_edge.
@@ -34,26 +34,6 @@ __device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long
   unsigned long long v;
   asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
-}
-
-__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
-__device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-__device__ __forceinline__ unsigned atom_add_acq_rel_u32(unsigned *p, unsigned v) {
-  unsigned o;
-  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(o) : "l"(p), "r"(v) : "memory");
-  return o;
-}
-
-__device__ __forceinline__ void st_relaxed_u32(unsigned *p, unsigned v) {
-  asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
 __device__ __forceinline__ int ld_volatile_i32(const int *p) { return *(volatile const int *)p; }
@@ -98,11 +78,12 @@ struct Key<DAWN_W_I32> {
   static __device__ __forceinline__ uint32_t out(uint32_t k) { return k ^ 0x80000000u; }
 };
 
+constexpr int32_t kMark = 0x100;  // above every entry index of a tile (at most kTile)
+
 struct WarpTile {
-  uint32_t rs[kTile + 1];    // CSR row start of each entry overlapping the tile
-  uint32_t off[kTile + 1];   // virtual offset of each entry's first edge
-  uint32_t dkey[kTile + 1];  // distance key of each entry's vertex
-  int32_t own[kTile];        // owning entry (relative index) of every virtual edge
+  uint32_t ebase[kTile + 1];  // per entry: CSR index of its edge at virtual offset 0 (mod 2^32)
+  uint32_t dkey[kTile + 1];   // per entry: current distance key of its vertex
+  int32_t own[kTile];         // owning entry (relative index) of every virtual edge
 };
 
 struct BlockShared {
@@ -110,18 +91,38 @@ struct BlockShared {
   unsigned long long scan[kWarpsPerBlock];
   unsigned long long base;
   int32_t flag;
+  unsigned long long bar_target;  // arrivals that end the next device-wide barrier (thread 0)
   WarpTile wt[kWarpsPerBlock];
 };
 
-__device__ __forceinline__ void set_status(DeviceCtl *ctl, int code) { atomicCAS(&ctl->status, 0, code); }
+constexpr unsigned long long kBarError = 1ull << 63;
 
-// Device-wide barrier with a bounded wait.  Returns false (uniformly for the
-// block) when the status word reports an error or the wait ran out.  The
-// arrival is an acquire-release add (it publishes the block's writes, ordered
-// before it by the block barrier); the last arrival resets the counter and
-// publishes the new generation with a release store that every waiter
-// acquires.
-__device__ bool grid_barrier(DeviceCtl *ctl, unsigned long long limit_ns, int32_t *s_flag) {
+__device__ __noinline__ void set_status(DeviceCtl *ctl, int code) {
+  atomicCAS(&ctl->status, 0, code);
+  atomicOr(&ctl->bar, kBarError);
+}
+
+__device__ __forceinline__ unsigned long long atom_add_acq_rel_u64(unsigned long long *p, unsigned long long v) {
+  unsigned long long o;
+  asm volatile("atom.acq_rel.gpu.global.add.u64 %0, [%1], %2;" : "=l"(o) : "l"(p), "l"(v) : "memory");
+  return o;
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Device-wide barrier with a bounded wait on a monotonic arrival counter:
+// barrier number b ends when the counter reaches b * gridDim.x, so no block
+// resets it or publishes a generation (one atomic per block and one poll per
+// waiter are all the barrier costs).  The arrival is an acquire-release add
+// (it publishes the block's writes, ordered before it by the block barrier);
+// waiters acquire the counter.  Any error sets bit 63 of the counter as well
+// as the status word, which releases every waiter at once.  Returns false
+// (uniformly for the block) on an error or when the wait ran out.
+__device__ bool grid_barrier(DeviceCtl *ctl, unsigned long long limit_ns, int32_t *s_flag, unsigned long long *s_target) {
   if (gridDim.x == 1) {  // one block: the block barrier already orders its memory operations
     __syncthreads();
     if (threadIdx.x == 0) *s_flag = ld_volatile_i32(&ctl->status) == 0;
@@ -130,25 +131,23 @@ __device__ bool grid_barrier(DeviceCtl *ctl, unsigned long long limit_ns, int32_
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    const unsigned gen = ld_acquire_u32(&ctl->bar_gen);
-    const unsigned arrived = atom_add_acq_rel_u32(&ctl->bar_count, 1u);
-    if (arrived == gridDim.x - 1) {
-      st_relaxed_u32(&ctl->bar_count, 0u);
-      st_release_u32(&ctl->bar_gen, gen + 1);
-    } else {
-      unsigned long long t0 = global_ns();
+    const unsigned long long target = *s_target + gridDim.x;
+    *s_target = target;
+    unsigned long long v = atom_add_acq_rel_u64(&ctl->bar, 1ull) + 1ull;
+    if (!(v & kBarError) && v < target) {
+      const unsigned long long t0 = global_ns();
       unsigned ns = 16;
-      while (ld_acquire_u32(&ctl->bar_gen) == gen) {
-        if (ld_volatile_i32(&ctl->status) != 0) break;
-        if (global_ns() - t0 > limit_ns) {
-          set_status(ctl, DAWN_ERR_TIMEOUT);
-          break;
-        }
+      do {
         __nanosleep(ns);
         if (ns < 128) ns <<= 1;
-      }
+        v = ld_acquire_u64(&ctl->bar);
+        if (!(v & kBarError) && v < target && global_ns() - t0 > limit_ns) {
+          set_status(ctl, DAWN_ERR_TIMEOUT);
+          v = kBarError;
+        }
+      } while (!(v & kBarError) && v < target);
     }
-    *s_flag = ld_volatile_i32(&ctl->status) == 0;
+    *s_flag = !(v & kBarError);
   }
   __syncthreads();
   return *s_flag != 0;
@@ -234,11 +233,11 @@ __device__ __forceinline__ int32_t find_instance(const int32_t *tprefix, int32_t
 // every instance; consumes (clears) the bitmap.  Work is split into 32-word
 // chunks (1024 vertices) handed to warps round-robin; a warp ranks the marked
 // vertices of its chunk with a popcount scan and expands them in rounds of
-// 128 (four consecutive ranks per lane), so all row_ptr and state reads of a
-// round are in flight together and no block-wide synchronisation is needed.
-// One atomicAdd per round reserves the entries and their edge offsets.  The
-// distance key stored in an entry is read here: no relaxation runs between
-// this phase and the next relax phase.
+// 128 (four consecutive ranks per lane), so all row_ptr reads of a round are
+// in flight together and no block-wide synchronisation is needed.  One
+// atomicAdd per round reserves the entries and their edge offsets.  The tile
+// starts of a row spanning more than two tiles are written by the whole warp
+// (one such row per lane and round; hub rows hold thousands of tiles).
 constexpr int kBuildPerLane = 4;
 
 __device__ void build_frontier(const GovmParams &p, unsigned long long *tails_next, WarpTile &wt,
@@ -248,8 +247,8 @@ __device__ void build_frontier(const GovmParams &p, unsigned long long *tails_ne
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int64_t cpi = (p.words + 31) / 32;  // 32-word chunks per instance
   const int64_t chunks = cpi * p.k;
-  uint32_t *wbits = wt.rs;            // the relax tile buffers are free during the build
-  uint32_t *wstart = wt.off;
+  uint32_t *wbits = wt.ebase;  // the relax tile buffers are free during the build
+  uint32_t *wstart = wt.dkey;
   for (int64_t ch = gwarp; ch < chunks; ch += nwarps) {
     const int32_t inst = (int32_t)(ch / cpi);
     const int64_t w0 = (ch - (int64_t)inst * cpi) * 32;
@@ -275,7 +274,6 @@ __device__ void build_frontier(const GovmParams &p, unsigned long long *tails_ne
     __syncwarp();
     uint4 *q = p.queue + (size_t)inst * p.n;
     int32_t *tl = p.tiles + (size_t)inst * p.tiles_cap;
-    const unsigned long long *st = p.state + (size_t)inst * p.n;
     for (uint32_t r0 = 0; r0 < T; r0 += 32 * kBuildPerLane) {  // warp-uniform
       const uint32_t lo = r0 + lane * kBuildPerLane;
       const uint32_t hi = min(lo + kBuildPerLane, T);
@@ -304,12 +302,11 @@ __device__ void build_frontier(const GovmParams &p, unsigned long long *tails_ne
           }
         }
       }
-      uint32_t rs[kBuildPerLane], d[kBuildPerLane], key[kBuildPerLane];
+      uint32_t rs[kBuildPerLane], d[kBuildPerLane];
 #pragma unroll
       for (int i = 0; i < kBuildPerLane; ++i) {
         rs[i] = v[i] >= 0 ? (uint32_t)__ldg(p.row_ptr + v[i]) : 0u;
         d[i] = v[i] >= 0 ? (uint32_t)__ldg(p.row_ptr + v[i] + 1) : 0u;
-        key[i] = v[i] >= 0 ? (uint32_t)(ld_relaxed_u64(st + v[i]) >> 32) : 0u;
       }
       uint32_t cnt = 0, degsum = 0;
 #pragma unroll
@@ -333,6 +330,7 @@ __device__ void build_frontier(const GovmParams &p, unsigned long long *tails_ne
       const unsigned long long pos = base + pre - mine;
       uint32_t idx = (uint32_t)pos;
       uint32_t off = (uint32_t)(pos >> 32);
+      uint32_t lb0 = 0, lb1 = 0, lidx = 0;  // this lane's first long entry, written by the warp
 #pragma unroll
       for (int i = 0; i < kBuildPerLane; ++i) {
         if (d[i] == 0) continue;
@@ -340,17 +338,31 @@ __device__ void build_frontier(const GovmParams &p, unsigned long long *tails_ne
           set_status(p.ctl, DAWN_ERR_BOUNDS);
           break;
         }
-        q[idx] = make_uint4(rs[i], off, key[i], (uint32_t)v[i]);
-        const uint32_t end = off + d[i];
-        for (uint32_t tb = (off + kTile - 1) / kTile; tb * (uint32_t)kTile < end; ++tb) {
-          if (tb >= (uint32_t)p.tiles_cap) {
-            set_status(p.ctl, DAWN_ERR_BOUNDS);
-            break;
-          }
-          tl[tb] = (int32_t)idx;
+        q[idx] = make_uint4(rs[i], off, rs[i] - off, (uint32_t)v[i]);
+        const uint32_t tb0 = (off + kTile - 1) / kTile;
+        uint32_t tb1 = (off + d[i] + kTile - 1) / kTile;
+        if (tb1 > (uint32_t)p.tiles_cap) {
+          set_status(p.ctl, DAWN_ERR_BOUNDS);
+          tb1 = max(tb0, (uint32_t)p.tiles_cap);
+        }
+        if (tb1 - tb0 > 2 && lb1 == 0) {
+          lb0 = tb0;
+          lb1 = tb1;
+          lidx = idx;
+        } else {
+          for (uint32_t tb = tb0; tb < tb1; ++tb) tl[tb] = (int32_t)idx;
         }
         ++idx;
-        off = end;
+        off += d[i];
+      }
+      unsigned bal = __ballot_sync(kFull, lb1 != 0);
+      while (bal) {
+        const int src = __ffs(bal) - 1;
+        bal &= bal - 1;
+        const uint32_t b0 = __shfl_sync(kFull, lb0, src);
+        const uint32_t b1 = __shfl_sync(kFull, lb1, src);
+        const int32_t ix = (int32_t)__shfl_sync(kFull, lidx, src);
+        for (uint32_t tb = b0 + lane; tb < b1; tb += 32) tl[tb] = ix;
       }
     }
   }
@@ -380,23 +392,41 @@ __device__ __forceinline__ void relax_tile(const GovmParams &p, WarpTile &wt, in
     if (lane == 0) set_status(p.ctl, DAWN_ERR_BOUNDS);
     return;
   }
-  for (int s = lane; s < kTile; s += 32) wt.own[s] = 0;
-  __syncwarp();
-  for (int32_t j = lane; j < nent; j += 32) {
+  // A tile inside one long row needs no owner search (hub rows of skewed
+  // degree distributions are mostly such tiles).
+  const bool one = nent == 1;
+  // Entries lane and lane + 32 are loaded together.  Each entry's distance
+  // key alpha[v] is read in place, as Algorithm 2 does (improvements made
+  // earlier in this step are used at once); those reads are consumed only
+  // after the edge loads below have been issued.  An entry's start marks
+  // own[] with kMark | j: every value left there by an earlier tile is below
+  // kMark, so the marks need no clearing.
+  const int32_t j0 = lane, j1 = lane + 32;
+  uint4 e0 = make_uint4(0u, 0u, 0u, 0u), e1 = e0;
+  if (j0 < nent) e0 = __ldcg(q + ia + j0);
+  if (j1 < nent) e1 = __ldcg(q + ia + j1);
+  unsigned long long f0 = ~0ull, f1 = ~0ull;
+  if (j0 < nent) {
+    wt.ebase[j0] = e0.z;
+    if (j0 > 0 && e0.y >= x0 && e0.y < x0 + (uint32_t)kTile) wt.own[e0.y - x0] = kMark | j0;
+    f0 = ld_relaxed_u64(st + e0.w);
+  }
+  if (j1 < nent) {
+    wt.ebase[j1] = e1.z;
+    if (e1.y >= x0 && e1.y < x0 + (uint32_t)kTile) wt.own[e1.y - x0] = kMark | j1;
+    f1 = ld_relaxed_u64(st + e1.w);
+  }
+  for (int32_t j = lane + 64; j < nent; j += 32) {  // tiles of many short rows
     const uint4 en = __ldcg(q + ia + j);
-    wt.rs[j] = en.x;
-    wt.off[j] = en.y;
-    // alpha[j] is read in place, as Algorithm 2 does: improvements made
-    // earlier in this step are used at once (never worse than the key stored
-    // when the frontier was built)
-    wt.dkey[j] = min(en.z, (uint32_t)(ld_relaxed_u64(st + en.w) >> 32));
-    if (j > 0 && en.y >= x0 && en.y < x0 + (uint32_t)kTile) wt.own[en.y - x0] = j;
+    wt.ebase[j] = en.z;
+    wt.dkey[j] = (uint32_t)(ld_relaxed_u64(st + en.w) >> 32);
+    if (en.y >= x0 && en.y < x0 + (uint32_t)kTile) wt.own[en.y - x0] = kMark | j;
   }
   __syncwarp();
   // Inclusive max-scan of entry starts: own[s] = entry owning edge x0 + s.
-  {
+  if (!one) {
     int32_t vals[kEdgesPerLane];
-    int32_t run = 0;
+    int32_t run = kMark;
 #pragma unroll
     for (int q2 = 0; q2 < kEdgesPerLane; ++q2) {
       run = max(run, wt.own[lane * kEdgesPerLane + q2]);
@@ -409,10 +439,10 @@ __device__ __forceinline__ void relax_tile(const GovmParams &p, WarpTile &wt, in
       if (lane >= d) incl = max(incl, o);
     }
     int32_t excl = __shfl_up_sync(kFull, incl, 1);
-    if (lane == 0) excl = 0;
+    if (lane == 0) excl = kMark;
     __syncwarp();
 #pragma unroll
-    for (int q2 = 0; q2 < kEdgesPerLane; ++q2) wt.own[lane * kEdgesPerLane + q2] = max(vals[q2], excl);
+    for (int q2 = 0; q2 < kEdgesPerLane; ++q2) wt.own[lane * kEdgesPerLane + q2] = max(vals[q2], excl) & (kMark - 1);
   }
   __syncwarp();
 
@@ -427,8 +457,8 @@ __device__ __forceinline__ void relax_tile(const GovmParams &p, WarpTile &wt, in
     const uint32_t x = x0 + r * 32 + lane;
     eidx[r] = 0;
     if (x < xend) {
-      const int32_t j = wt.own[r * 32 + lane];
-      const uint32_t e = wt.rs[j] + (x - wt.off[j]);
+      const int32_t j = one ? 0 : wt.own[r * 32 + lane];
+      const uint32_t e = x + wt.ebase[j];
       if (e < (uint32_t)p.m) {
         valid |= 1u << r;
         eidx[r] = e;
@@ -446,6 +476,9 @@ __device__ __forceinline__ void relax_tile(const GovmParams &p, WarpTile &wt, in
 #pragma unroll
   for (int r = 0; r < kEdgesPerLane; ++r)
     curst[r] = (valid & (1u << r)) ? ld_relaxed_u64(st + cw[r].x) : 0ull;
+  if (j0 < nent) wt.dkey[j0] = (uint32_t)(f0 >> 32);
+  if (j1 < nent) wt.dkey[j1] = (uint32_t)(f1 >> 32);
+  __syncwarp();
   // Relax.  A candidate that beats the distance read marks beta (the thread
   // whose atomicMin strictly lowers a distance always read a larger value, so
   // every strict improvement is marked); equal-distance candidates with a
@@ -454,7 +487,7 @@ __device__ __forceinline__ void relax_tile(const GovmParams &p, WarpTile &wt, in
   unsigned need = 0;
 #pragma unroll
   for (int r = 0; r < kEdgesPerLane; ++r) {
-    ckey[r] = Key<WT>::add(wt.dkey[wt.own[r * 32 + lane]], cw[r].y);
+    ckey[r] = Key<WT>::add(wt.dkey[one ? 0 : wt.own[r * 32 + lane]], cw[r].y);
     const unsigned long long cand = ((unsigned long long)ckey[r] << 32) | eidx[r];
     if ((valid & (1u << r)) && cand < curst[r] && curst[r] != kSourceState) need |= 1u << r;
   }
@@ -487,6 +520,9 @@ __global__ void __launch_bounds__(kBlockThreads, 5) govm_kernel(GovmParams p) {
   const unsigned long long kSourceState = ((unsigned long long)Key<WT>::zero << 32) | kNoEdge;
   unsigned long long updates = 0;  // vertices entering beta, summed over steps
   unsigned long long seeded = 0;   // the seeds' own marks (not path updates)
+  if (tid == 0) sh.bar_target = 0;
+  for (int s = lane; s < kTile; s += 32) sh.wt[warp].own[s] = 0;
+  __syncwarp();
   long long step = 0;
   bool quiescent = false;
 
@@ -510,7 +546,7 @@ __global__ void __launch_bounds__(kBlockThreads, 5) govm_kernel(GovmParams p) {
   }
   for (long long i = gtid; i < (long long)p.k * p.words; i += gsize) p.bitmap[i] = 0u;
   for (long long i = gtid; i < 2LL * p.k; i += gsize) p.tails[i] = 0ull;
-  if (!grid_barrier(ctl, p.wait_limit_ns, &sh.flag)) goto finish;
+  if (!grid_barrier(ctl, p.wait_limit_ns, &sh.flag, &sh.bar_target)) goto finish;
 
   // 2. Seeds: alpha[s] = 0, s enters beta.
   for (long long i = gtid; i < (p.roots_mode ? (long long)p.nseeds : (long long)p.k); i += gsize) {
@@ -523,9 +559,9 @@ __global__ void __launch_bounds__(kBlockThreads, 5) govm_kernel(GovmParams p) {
     p.state[(size_t)inst * p.n + s] = kSourceState;
     atomicOr(p.bitmap + (size_t)inst * p.words + (s >> 5), 1u << (s & 31));
   }
-  if (!grid_barrier(ctl, p.wait_limit_ns, &sh.flag)) goto finish;
+  if (!grid_barrier(ctl, p.wait_limit_ns, &sh.flag, &sh.bar_target)) goto finish;
   build_frontier(p, p.tails, sh.wt[warp], seeded);
-  if (!grid_barrier(ctl, p.wait_limit_ns, &sh.flag)) goto finish;
+  if (!grid_barrier(ctl, p.wait_limit_ns, &sh.flag, &sh.bar_target)) goto finish;
 
   // 3. GOVM steps.
   for (;; ++step) {
@@ -575,10 +611,10 @@ __global__ void __launch_bounds__(kBlockThreads, 5) govm_kernel(GovmParams p) {
       relax_tile<WT>(p, sh.wt[warp], inst, g - sh.tprefix[inst], __ldcg(tails_cur + inst),
                       sh.tprefix[inst + 1] - sh.tprefix[inst], p.gsvm ? &ctl->changed[step % 3] : nullptr);
     }
-    if (!grid_barrier(ctl, p.wait_limit_ns, &sh.flag)) break;
+    if (!grid_barrier(ctl, p.wait_limit_ns, &sh.flag, &sh.bar_target)) break;
     // build the next frontier
     build_frontier(p, tails_next, sh.wt[warp], updates);
-    if (!grid_barrier(ctl, p.wait_limit_ns, &sh.flag)) break;
+    if (!grid_barrier(ctl, p.wait_limit_ns, &sh.flag, &sh.bar_target)) break;
   }
 
   if (quiescent && blockIdx.x == 0 && tid == 0 && p.trace && step < p.trace_cap) {
