@@ -179,6 +179,12 @@ def run_sssp_bench(args, wl, device, world, rank):
     stream = torch.cuda.current_stream()
     g = dawn.Graph(wl.row_ptr, wl.col, wl.weights, device=device)
     S = len(wl.sources)
+    tuning = None
+    if not args.no_tune:  # launch shape picked by the library's autotuner (untimed setup, like the upload)
+        t = time.perf_counter()
+        tuning = g.autotune(wl.sources[:min(8, S)], mode="sssp", reps=2)
+        tuning["tune_s"] = time.perf_counter() - t
+        log(f"[bench] autotune: {tuning}")
     dist = torch.empty((S, wl.n), dtype=g.dist_dtype, device=device)
     par = torch.empty((S, wl.n), dtype=torch.int32, device=device)
     srcs = [int(s) for s in wl.sources]
@@ -225,6 +231,7 @@ def run_sssp_bench(args, wl, device, world, rank):
     achieved_gbs_total = float(b_alg.sum() / (per_src_ms.sum() / 1e3) / 1e9)
     mu = float(np.mean([st["updates"] for st in stats]))
     res = {
+        "tuning": tuning,
         "elapsed": elapsed,
         "gteps": S * args.steps * world * wl.e_wcc / elapsed / 1e9,
         "launch_ms_mean": float(launch_ms.mean()),
@@ -247,11 +254,11 @@ def run_sssp_bench(args, wl, device, world, rank):
     return res
 
 
-def run_e2e(args, wl, device, world):
+def run_e2e(args, wl, device, world, tuning=None):
     """Same metric through the C ABI from pinned host buffers: per step the
     graph is copied in and validated (dawn_create_graph with host inputs),
-    every source is solved, and dist + parent are copied back to pinned
-    host memory."""
+    the tuned launch options are set, every source is solved, and dist +
+    parent are copied back to pinned host memory."""
     import torch
     import paper_2306_07872_gb300 as dawn
 
@@ -270,6 +277,9 @@ def run_e2e(args, wl, device, world):
 
     def step():
         h = dawn.dawn_create_graph(rp, cl, w, stream)
+        if tuning:
+            dawn.dawn_set_option(h, dawn.DAWN_OPT_CTAS_PER_SM, tuning["ctas_per_sm"])
+            dawn.dawn_set_option(h, dawn.DAWN_OPT_GRID_BLOCKS, tuning["grid_blocks"])
         for i, s in enumerate(srcs):
             dawn.dawn_sssp(h, s, dist[i], par[i], None, stream)
         h_dist.copy_(dist, non_blocking=True)
@@ -348,10 +358,13 @@ def run_batched(args):
     dist = torch.empty((k, wl.n), dtype=torch.uint32, device="cuda")
     par = torch.empty((k, wl.n), dtype=torch.int32, device="cuda")
     dawn.dawn_reserve(g.handle, k)
+    tune_batch = None if args.no_tune else g.autotune(wl.sources, mode="msssp", reps=2)
     t_batch = _time(lambda: dawn.dawn_msssp(g.handle, src, dist, par))
     g.check()
     st = g.stats()
     srcs = [int(x) for x in wl.sources]
+    # the loop arm gets its own tuned launch shape
+    tune_loop = None if args.no_tune else g.autotune(wl.sources[:8], mode="sssp", reps=2)
     def loop():
         for i, s_ in enumerate(srcs):
             dawn.dawn_sssp(g.handle, s_, dist[i], par[i], None)
@@ -361,7 +374,8 @@ def run_batched(args):
                                 "gteps_batched": k * wl.e_wcc / t_batch / 1e9,
                                 "gteps_loop": k * wl.e_wcc / t_loop / 1e9,
                                 "edges_scanned_per_instance": st["edges_scanned"] / k,
-                                "updates_per_instance": st["updates"] / k}
+                                "updates_per_instance": st["updates"] / k,
+                                "tuning_batched": tune_batch, "tuning_loop": tune_loop}
     del dist, par
     g.close()
     torch.cuda.empty_cache()
@@ -370,6 +384,7 @@ def run_batched(args):
     roots = torch.from_numpy(wb.sources).cuda()
     du = torch.empty(wb.n, dtype=torch.uint32, device="cuda")
     pu = torch.empty(wb.n, dtype=torch.int32, device="cuda")
+    tune_roots = None if args.no_tune else gu.autotune(wb.sources, mode="roots", reps=2)
     t_roots = _time(lambda: dawn.dawn_sssp_roots(gu.handle, roots, du, pu))
     gu.check()
     offs = wb.extra["offsets"]
@@ -379,6 +394,8 @@ def run_batched(args):
         e0, e1 = int(wb.row_ptr[a]), int(wb.row_ptr[b])
         rp = (wb.row_ptr[a:b + 1] - e0).astype(np.int32)
         parts.append(dawn.Graph(rp, (wb.col[e0:e1] - a).astype(np.int32), wb.weights[e0:e1]))
+        if not args.no_tune:
+            parts[-1].autotune([0], mode="sssp", reps=1)
     outs = [(torch.empty(p_.n, dtype=torch.uint32, device="cuda"), torch.empty(p_.n, dtype=torch.int32, device="cuda"))
             for p_ in parts]
     def loop2():
@@ -389,7 +406,7 @@ def run_batched(args):
         p_.check()
     out["roots_er64"] = {"one_launch_s": t_roots, "loop_s": t_loop2, "speedup": t_loop2 / t_roots,
                          "gteps_one_launch": wb.m / t_roots / 1e9, "gteps_loop": wb.m / t_loop2 / 1e9,
-                         "n": wb.n, "m": wb.m}
+                         "n": wb.n, "m": wb.m, "tuning_one_launch": tune_roots}
     for p_ in parts:
         p_.close()
     gu.close()
@@ -606,7 +623,7 @@ def main_ours(args):
         res = run_sssp_bench(args, wl, device, world, rank)
         log(f"[bench] device: {res['gteps']:.2f} GTEPS, {res['launch_ms_mean']:.3f} ms/launch, "
             f"B_alg {res['b_alg_mean'] / 1e9:.3f} GB, {res['achieved_gbs']:.0f} GB/s, steps {res['steps_mean']:.1f}")
-        e2e = run_e2e(args, wl, device, world) if not args.no_e2e else None
+        e2e = run_e2e(args, wl, device, world, res["tuning"]) if not args.no_e2e else None
         cpu = cpu_baseline(wl, args.cpu_budget) if (rank == 0 and not args.no_cpu) else None
         if rank != 0:
             return
@@ -629,6 +646,7 @@ def main_ours(args):
                        "edges_scanned_mean": res["edges_scanned_mean"],
                        "edges_scanned_over_e_wcc": res["edges_scanned_mean"] / wl.e_wcc},
             "e2e": e2e, "gpu_launches": res["launches"], "clocks": res["clocks"], "cpu_baseline": cpu,
+            "tuning": res["tuning"],
         }
         print(json.dumps(line), flush=True)
     elif args.workload in ("batched", "diff", "mu", "apsp", "gsvm"):
@@ -650,6 +668,7 @@ def main():
     ap.add_argument("--workload", default="rmat22")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="keep the default launch shape (no autotuning)")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--sources", type=int, default=0, help="limit sources per step (profiling runs)")
     args = ap.parse_args()

@@ -184,7 +184,15 @@ int dawn_get_stats(dawn_graph g, dawn_stats *out);
  * Tuning and test options.
  *   DAWN_OPT_MAX_STEPS     step cap (default n, as in "while step < n")
  *   DAWN_OPT_WAIT_LIMIT_NS bound on every in-kernel wait (default 4e9 ns)
- *   DAWN_OPT_GRID_BLOCKS   persistent grid size (0 = all co-resident blocks)
+ *   DAWN_OPT_GRID_BLOCKS   persistent grid size (0 = automatic: all
+ *                          co-resident CTAs for large problems, fewer for
+ *                          small ones; larger values are clamped to the
+ *                          co-resident count)
+ *   DAWN_OPT_CTAS_PER_SM   kernel build: 5 (the default; 48 registers per
+ *                          thread, 40 resident warps per SM) or 4 (64
+ *                          registers, 32 warps); 0 = default, others invalid
+ *   DAWN_OPT_BATCH         instances per persistent launch in dawn_msssp
+ *                          (0 = as many as the workspace budget allows)
  *   DAWN_OPT_TEST_STALL    1: block 0 waits on a flag nothing sets, so the
  *                          bounded waits run out (tests DAWN_ERR_TIMEOUT)
  *   DAWN_OPT_TRACE_STEPS   record up to `value` per-step trace rows in later
@@ -202,9 +210,51 @@ enum {
   DAWN_OPT_GRID_BLOCKS = 3,
   DAWN_OPT_TEST_STALL = 4,
   DAWN_OPT_TRACE_STEPS = 5,
-  DAWN_OPT_GSVM = 6
+  DAWN_OPT_GSVM = 6,
+  DAWN_OPT_CTAS_PER_SM = 7,
+  DAWN_OPT_BATCH = 8
 };
 int dawn_set_option(dawn_graph g, int option, int64_t value);
+
+/*
+ * Launch autotuner (the paper has no counterpart; it picks this library's
+ * launch shape for a given graph and workload).
+ *
+ * Times the workload under candidate launch configurations and stores the
+ * fastest as the handle's options (DAWN_OPT_CTAS_PER_SM, DAWN_OPT_GRID_BLOCKS
+ * and, in DAWN_TUNE_MSSSP mode, DAWN_OPT_BATCH), which then apply to every
+ * later solve on the handle.  The candidates are the two kernel builds
+ * (4 or 5 CTAs per SM) times the grid sizes {all co-resident CTAs, 3/4, 1/2,
+ * 1/4 of them, one per SM, the automatic size}, times, in DAWN_TUNE_MSSSP
+ * mode, the batch sizes {largest, 1/2, 1/4 of it}.  Results do not depend on
+ * the configuration (the solver's fixpoint is order-independent); only the
+ * time does.
+ *   mode     DAWN_TUNE_SSSP: dawn_sssp from each source in turn;
+ *            DAWN_TUNE_MSSSP: one dawn_msssp over all k sources;
+ *            DAWN_TUNE_ROOTS: one dawn_sssp_roots with the k sources as roots
+ *   sources  HOST array of k vertex ids (each in [0, n))
+ *   reps     timed repetitions per candidate after one warm-up (<= 0: 3);
+ *            the score is the median
+ *   out      receives the chosen configuration and its timing (may be NULL)
+ * The call is synchronous: it waits for `stream` and allocates scratch
+ * output buffers for its duration (DAWN_TUNE_MSSSP: up to 4 GiB, the
+ * sources beyond that are not part of the timed workload), so it must not
+ * be issued during stream capture.  On an error the options in force
+ * before the call are restored and the error is returned.
+ */
+typedef struct {
+  int32_t ctas_per_sm;  /* chosen kernel build (4 or 5) */
+  int32_t grid_blocks;  /* chosen DAWN_OPT_GRID_BLOCKS (0 = the automatic size) */
+  int32_t batch;        /* chosen DAWN_OPT_BATCH (0 = automatic; always 0 outside DAWN_TUNE_MSSSP) */
+  int32_t candidates;   /* configurations timed */
+  float best_ms;        /* median workload time with the chosen configuration */
+  float default_ms;     /* median workload time with the default options */
+} dawn_tuning;
+
+enum { DAWN_TUNE_SSSP = 0, DAWN_TUNE_MSSSP = 1, DAWN_TUNE_ROOTS = 2 };
+
+int dawn_autotune(dawn_graph g, int mode, const int32_t *sources, int32_t k, int32_t reps, void *stream,
+                  dawn_tuning *out);
 
 /*
  * Per-step trace of the last solve (enable with DAWN_OPT_TRACE_STEPS; waits

@@ -41,9 +41,11 @@ struct dawn_graph_s {
   int64_t max_steps = 0;
   unsigned long long wait_limit_ns = 4000000000ull;
   int grid_blocks = 0;
+  int ctas_per_sm = 0;  // kernel build (0 = default)
+  int batch = 0;        // instances per msssp launch (0 = automatic)
   int test_stall = 0;
   int gsvm = 0;
-  int blocks_per_sm = 0;  // co-resident persistent blocks per SM (cached)
+  int occupancy[2] = {0, 0};  // co-resident CTAs per SM of the 4- and 5-CTA builds (cached)
   int last_k = 0;
   cudaStream_t last_stream = nullptr;
 };
@@ -209,10 +211,16 @@ int ensure_workspace(dawn_graph g, int32_t k) {
   return DAWN_OK;
 }
 
+int kernel_ctas(dawn_graph g) { return g->ctas_per_sm == 4 ? 4 : 5; }
+
+int occupancy(dawn_graph g, int ctas) {
+  int &c = g->occupancy[ctas == 4 ? 0 : 1];
+  if (c == 0) c = std::max(1, dawn::govm_max_blocks_per_sm(g->wtype, ctas));
+  return c;
+}
+
 int grid_for(dawn_graph g, int32_t k) {
-  if (g->blocks_per_sm == 0) g->blocks_per_sm = std::max(1, dawn::govm_max_blocks_per_sm(g->wtype));
-  const int per_sm = g->blocks_per_sm;
-  const int cap = per_sm * g->sms;
+  const int cap = occupancy(g, kernel_ctas(g)) * g->sms;
   if (g->grid_blocks > 0) return std::min(g->grid_blocks, cap);
   // small problems get a small grid: barriers are cheaper with fewer blocks
   const int64_t work = (int64_t)k * std::max<int64_t>(g->m, g->n);
@@ -256,7 +264,7 @@ int run_solve(dawn_graph g, const int32_t *seeds, int32_t nseeds, int32_t source
   if (e == cudaSuccess && g->trace)
     e = cudaMemsetAsync(g->trace, 0, (size_t)g->trace_cap * 4 * sizeof(unsigned long long), stream);
   if (e != cudaSuccess) return cuda_fail(e);
-  e = dawn::launch_govm(p, g->wtype, grid_for(g, k), stream);
+  e = dawn::launch_govm(p, g->wtype, kernel_ctas(g), grid_for(g, k), stream);
   if (e != cudaSuccess) return cuda_fail(e);
   g->last_stream = stream;
   return DAWN_OK;
@@ -310,6 +318,21 @@ void release(dawn_graph g) {
 }
 
 }  // namespace
+
+namespace dawn {
+int launch_limits(dawn_graph g, LaunchLimits *out) {
+  if (!g || !out) return DAWN_ERR_INVALID;
+  if (set_device(g)) return DAWN_ERR_CUDA;
+  out->sms = g->sms;
+  out->occupancy4 = occupancy(g, 4);
+  out->occupancy5 = occupancy(g, 5);
+  out->max_batch = max_chunk(g);
+  out->ctas_per_sm = g->ctas_per_sm;
+  out->grid_blocks = g->grid_blocks;
+  out->batch = g->batch;
+  return DAWN_OK;
+}
+}  // namespace dawn
 
 extern "C" {
 
@@ -405,7 +428,9 @@ int dawn_sssp(dawn_graph g, int32_t source, void *dist, int32_t *parent, int32_t
 int dawn_msssp(dawn_graph g, const int32_t *sources, int32_t k, void *dist, int32_t *parent, void *stream) {
   if (!g || !sources || !dist || k < 1) return DAWN_ERR_INVALID;
   if (set_device(g)) return DAWN_ERR_CUDA;
-  const int32_t chunk = std::min(k, g->ws_k > 0 ? std::max(g->ws_k, std::min(k, max_chunk(g))) : max_chunk(g));
+  const int32_t chunk = g->batch > 0 ? std::min({k, g->batch, max_chunk(g)})
+                                     : std::min(k, g->ws_k > 0 ? std::max(g->ws_k, std::min(k, max_chunk(g)))
+                                                               : max_chunk(g));
   g->last_k = k;
   for (int32_t b = 0; b < k; b += chunk) {
     const int32_t kk = std::min(chunk, k - b);
@@ -478,6 +503,14 @@ int dawn_set_option(dawn_graph g, int option, int64_t value) {
     case DAWN_OPT_GRID_BLOCKS:
       if (value < 0) return DAWN_ERR_INVALID;
       g->grid_blocks = (int)value;
+      return DAWN_OK;
+    case DAWN_OPT_CTAS_PER_SM:
+      if (value != 0 && value != 4 && value != 5) return DAWN_ERR_INVALID;
+      g->ctas_per_sm = (int)value;
+      return DAWN_OK;
+    case DAWN_OPT_BATCH:
+      if (value < 0 || value > 0x7FFFFFFF) return DAWN_ERR_INVALID;
+      g->batch = (int)value;
       return DAWN_OK;
     case DAWN_OPT_TEST_STALL: g->test_stall = value != 0; return DAWN_OK;
     case DAWN_OPT_GSVM: g->gsvm = value != 0; return DAWN_OK;
@@ -629,7 +662,7 @@ extern "C" int dawn_sssp_noalloc(dawn_graph g, int32_t source, void *dist, int32
   // the control block (barrier counters, status) must start at zero; the
   // kernel itself resets everything else it reads
   cudaError_t e = cudaMemsetAsync(ctl, 0, sizeof(DeviceCtl), s);
-  if (e == cudaSuccess) e = dawn::launch_govm(p, g->wtype, grid_for(g, 1), s);
+  if (e == cudaSuccess) e = dawn::launch_govm(p, g->wtype, kernel_ctas(g), grid_for(g, 1), s);
   if (e == cudaSuccess && status_out)
     e = cudaMemcpyAsync(status_out, &ctl->status, sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
   if (e != cudaSuccess) return cuda_fail(e);

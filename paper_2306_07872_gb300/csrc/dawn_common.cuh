@@ -86,7 +86,23 @@ struct GovmParams {
 };
 
 // Host-side launchers (govm_kernel.cu).
-cudaError_t launch_govm(const GovmParams &p, int wtype, int grid_blocks, cudaStream_t stream);
-int govm_max_blocks_per_sm(int wtype);
+// ctas_per_sm selects the kernel build (4 or 5 resident CTAs per SM; any
+// other value means 5).  The launch is cooperative: grid_blocks must not
+// exceed govm_max_blocks_per_sm(wtype, ctas_per_sm) times the SM count.
+cudaError_t launch_govm(const GovmParams &p, int wtype, int ctas_per_sm, int grid_blocks, cudaStream_t stream);
+int govm_max_blocks_per_sm(int wtype, int ctas_per_sm);
+
+// Launch limits and current launch options of a handle (dawn_api.cu), for
+// the autotuner (dawn_tune.cu), which otherwise uses only the public API.
+struct LaunchLimits {
+  int sms;              // streaming multiprocessors of the handle's device
+  int occupancy4;       // co-resident CTAs per SM of the 4-CTA kernel build
+  int occupancy5;       // same for the 5-CTA build
+  int32_t max_batch;    // most instances one msssp launch may hold
+  int ctas_per_sm;      // current DAWN_OPT_CTAS_PER_SM
+  int grid_blocks;      // current DAWN_OPT_GRID_BLOCKS
+  int batch;            // current DAWN_OPT_BATCH
+};
+int launch_limits(dawn_graph g, LaunchLimits *out);
 
 }  // namespace dawn

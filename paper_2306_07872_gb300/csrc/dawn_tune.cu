@@ -1,0 +1,164 @@
+// Launch autotuner: picks the kernel build (CTAs per SM), the persistent
+// grid size and the msssp batch size for one graph and workload by timing
+// candidates with CUDA events.  The paper has no counterpart (its launch
+// shape is fixed); every solve it times runs through the public API, so a
+// tuned configuration is exactly what later solves on the handle use.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "dawn_common.cuh"
+
+namespace {
+
+struct Candidate {
+  int ctas;   // DAWN_OPT_CTAS_PER_SM
+  int grid;   // DAWN_OPT_GRID_BLOCKS (0 = automatic)
+  int batch;  // DAWN_OPT_BATCH (0 = automatic)
+};
+
+// Restores a handle's launch options unless released.
+struct OptionGuard {
+  dawn_graph g;
+  int ctas, grid, batch;
+  bool armed = true;
+  ~OptionGuard() {
+    if (!armed) return;
+    dawn_set_option(g, DAWN_OPT_CTAS_PER_SM, ctas);
+    dawn_set_option(g, DAWN_OPT_GRID_BLOCKS, grid);
+    dawn_set_option(g, DAWN_OPT_BATCH, batch);
+  }
+};
+
+struct Scratch {
+  int32_t *sources = nullptr;
+  void *dist = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  ~Scratch() {
+    cudaFree(sources);
+    cudaFree(dist);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  }
+};
+
+int apply(dawn_graph g, const Candidate &c) {
+  int rc = dawn_set_option(g, DAWN_OPT_CTAS_PER_SM, c.ctas);
+  if (!rc) rc = dawn_set_option(g, DAWN_OPT_GRID_BLOCKS, c.grid);
+  if (!rc) rc = dawn_set_option(g, DAWN_OPT_BATCH, c.batch);
+  return rc;
+}
+
+// Grid sizes worth timing for one kernel build: all co-resident CTAs and
+// fractions of them, one CTA per SM, and the automatic size (0).
+std::vector<int> grid_candidates(int cap, int sms) {
+  std::vector<int> v = {0};
+  for (int x : {cap, cap * 3 / 4, cap / 2, cap / 4, sms})
+    if (x >= 1 && x <= cap && std::find(v.begin(), v.end(), x) == v.end()) v.push_back(x);
+  return v;
+}
+
+// Batch sizes worth timing (msssp mode): the largest that fits, a half and
+// a quarter of it; sizes that give the same launches are timed once.
+std::vector<int> batch_candidates(int32_t k, int32_t max_batch) {
+  std::vector<int> v = {0};
+  std::vector<int32_t> seen = {std::min(k, max_batch)};
+  for (int32_t b : {max_batch / 2, max_batch / 4}) {
+    const int32_t eff = std::min(k, b);
+    if (b >= 1 && std::find(seen.begin(), seen.end(), eff) == seen.end()) {
+      seen.push_back(eff);
+      v.push_back((int)b);
+    }
+  }
+  return v;
+}
+
+}  // namespace
+
+extern "C" int dawn_autotune(dawn_graph g, int mode, const int32_t *sources, int32_t k, int32_t reps,
+                             void *stream, dawn_tuning *out) {
+  if (!g || !sources || k < 1 || mode < DAWN_TUNE_SSSP || mode > DAWN_TUNE_ROOTS) return DAWN_ERR_INVALID;
+  int32_t n = 0;
+  int64_t m = 0;
+  int wtype = 0;
+  int rc = dawn_graph_info(g, &n, &m, &wtype);
+  if (rc) return rc;
+  for (int32_t i = 0; i < k; ++i)
+    if (sources[i] < 0 || sources[i] >= n) return DAWN_ERR_INVALID;
+  dawn::LaunchLimits lim;
+  if ((rc = dawn::launch_limits(g, &lim))) return rc;
+  if (reps <= 0) reps = 3;
+  cudaStream_t s = (cudaStream_t)stream;
+
+  // The timed workload.  msssp mode keeps at most 4 GiB of distances.
+  int32_t kk = k;
+  if (mode == DAWN_TUNE_MSSSP) kk = (int32_t)std::max<int64_t>(1, std::min<int64_t>(k, ((int64_t)1 << 30) / n));
+  Scratch sc;
+  const size_t dist_rows = mode == DAWN_TUNE_MSSSP ? (size_t)kk : 1;
+  if (cudaMalloc((void **)&sc.sources, sizeof(int32_t) * (size_t)k) != cudaSuccess ||
+      cudaMalloc(&sc.dist, sizeof(uint32_t) * dist_rows * (size_t)n) != cudaSuccess ||
+      cudaEventCreate(&sc.e0) != cudaSuccess || cudaEventCreate(&sc.e1) != cudaSuccess) {
+    cudaGetLastError();
+    return DAWN_ERR_OOM;
+  }
+  if (cudaMemcpyAsync(sc.sources, sources, sizeof(int32_t) * (size_t)k, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return DAWN_ERR_CUDA;
+
+  auto workload = [&]() -> int {
+    if (mode == DAWN_TUNE_MSSSP) return dawn_msssp(g, sc.sources, kk, sc.dist, nullptr, s);
+    if (mode == DAWN_TUNE_ROOTS) return dawn_sssp_roots(g, sc.sources, k, sc.dist, nullptr, nullptr, s);
+    for (int32_t i = 0; i < k; ++i) {
+      const int r = dawn_sssp(g, sources[i], sc.dist, nullptr, nullptr, s);
+      if (r) return r;
+    }
+    return DAWN_OK;
+  };
+
+  // The default configuration comes first, so it wins ties.
+  std::vector<Candidate> cands;
+  const std::vector<int> batches =
+      mode == DAWN_TUNE_MSSSP ? batch_candidates(kk, lim.max_batch) : std::vector<int>{0};
+  for (int ctas : {5, 4}) {
+    const int cap = (ctas == 4 ? lim.occupancy4 : lim.occupancy5) * lim.sms;
+    for (int grid : grid_candidates(cap, lim.sms))
+      for (int batch : batches) cands.push_back({ctas, grid, batch});
+  }
+
+  OptionGuard guard{g, lim.ctas_per_sm, lim.grid_blocks, lim.batch};
+  float best_ms = 0.0f, default_ms = 0.0f;
+  size_t best = 0;
+  std::vector<float> t(reps);
+  for (size_t c = 0; c < cands.size(); ++c) {
+    if ((rc = apply(g, cands[c]))) return rc;
+    if ((rc = workload())) return rc;  // warm-up (and workspace growth)
+    for (int32_t r = 0; r < reps; ++r) {
+      if (cudaEventRecord(sc.e0, s) != cudaSuccess) return DAWN_ERR_CUDA;
+      if ((rc = workload())) return rc;
+      if (cudaEventRecord(sc.e1, s) != cudaSuccess || cudaEventSynchronize(sc.e1) != cudaSuccess ||
+          cudaEventElapsedTime(&t[r], sc.e0, sc.e1) != cudaSuccess)
+        return DAWN_ERR_CUDA;
+    }
+    if ((rc = dawn_status(g, 1))) return rc;
+    std::nth_element(t.begin(), t.begin() + reps / 2, t.end());
+    const float med = t[reps / 2];
+    if (c == 0) default_ms = med;
+    if (c == 0 || med < best_ms) {
+      best_ms = med;
+      best = c;
+    }
+  }
+  if ((rc = apply(g, cands[best]))) return rc;
+  guard.armed = false;
+  if (out) {
+    const Candidate &b = cands[best];
+    out->ctas_per_sm = b.ctas;
+    out->grid_blocks = b.grid;
+    out->batch = b.batch;
+    out->candidates = (int32_t)cands.size();
+    out->best_ms = best_ms;
+    out->default_ms = default_ms;
+  }
+  return DAWN_OK;
+}

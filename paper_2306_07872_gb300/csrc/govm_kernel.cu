@@ -508,8 +508,12 @@ __device__ __forceinline__ void relax_tile(const GovmParams &p, WarpTile &wt, in
   if (changed && __any_sync(kFull, strict != 0) && lane == 0) atomicOr(changed, 1u);
 }
 
-template <int WT>
-__global__ void __launch_bounds__(kBlockThreads, 5) govm_kernel(GovmParams p) {
+// MINB = CTAs per SM the build targets: 5 caps a thread at 48 registers
+// (40 resident warps per SM, the most latency hiding), 4 at 64 (no spills,
+// more loads in flight per warp).  Which is faster depends on the graph;
+// dawn_autotune picks it.
+template <int WT, int MINB>
+__global__ void __launch_bounds__(kBlockThreads, MINB) govm_kernel(GovmParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   BlockShared &sh = *reinterpret_cast<BlockShared *>(smem_raw);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -657,24 +661,35 @@ finish:
 }
 
 // Shared memory exceeds the 48 KB static limit: opt in once per kernel.
+using GovmFn = void (*)(GovmParams);
+
+template <int MINB>
+GovmFn kernel_for_wtype(int wtype) {
+  if (wtype == DAWN_W_F32) return govm_kernel<DAWN_W_F32, MINB>;
+  if (wtype == DAWN_W_I32) return govm_kernel<DAWN_W_I32, MINB>;
+  return govm_kernel<DAWN_W_U32, MINB>;
+}
+
+GovmFn kernel_for(int wtype, int ctas_per_sm) {
+  return ctas_per_sm == 4 ? kernel_for_wtype<4>(wtype) : kernel_for_wtype<5>(wtype);
+}
+
 cudaError_t prepare_kernels() {
   static bool done = false;
   if (done) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(govm_kernel<DAWN_W_U32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)sizeof(BlockShared));
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(govm_kernel<DAWN_W_F32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sizeof(BlockShared));
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(govm_kernel<DAWN_W_I32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)sizeof(BlockShared));
+  cudaError_t e = cudaSuccess;
+  for (int wtype : {DAWN_W_U32, DAWN_W_F32, DAWN_W_I32})
+    for (int c : {4, 5})
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kernel_for(wtype, c), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)sizeof(BlockShared));
   done = e == cudaSuccess;
   return e;
 }
 
 }  // namespace
 
-cudaError_t launch_govm(const GovmParams &p, int wtype, int grid_blocks, cudaStream_t stream) {
+cudaError_t launch_govm(const GovmParams &p, int wtype, int ctas_per_sm, int grid_blocks, cudaStream_t stream) {
   cudaError_t e = prepare_kernels();
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
@@ -687,19 +702,14 @@ cudaError_t launch_govm(const GovmParams &p, int wtype, int grid_blocks, cudaStr
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  if (wtype == DAWN_W_F32) return cudaLaunchKernelEx(&cfg, govm_kernel<DAWN_W_F32>, p);
-  if (wtype == DAWN_W_I32) return cudaLaunchKernelEx(&cfg, govm_kernel<DAWN_W_I32>, p);
-  return cudaLaunchKernelEx(&cfg, govm_kernel<DAWN_W_U32>, p);
+  return cudaLaunchKernelEx(&cfg, kernel_for(wtype, ctas_per_sm), p);
 }
 
-int govm_max_blocks_per_sm(int wtype) {
+int govm_max_blocks_per_sm(int wtype, int ctas_per_sm) {
   int nb = 0;
   if (prepare_kernels() != cudaSuccess) return 0;
-  const size_t smem = sizeof(BlockShared);
-  cudaError_t e =
-      wtype == DAWN_W_F32   ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, govm_kernel<DAWN_W_F32>, kBlockThreads, smem)
-      : wtype == DAWN_W_I32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, govm_kernel<DAWN_W_I32>, kBlockThreads, smem)
-                            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, govm_kernel<DAWN_W_U32>, kBlockThreads, smem);
+  const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel_for(wtype, ctas_per_sm),
+                                                                      kBlockThreads, sizeof(BlockShared));
   return e == cudaSuccess ? nb : 0;
 }
 

@@ -27,10 +27,12 @@ DAWN_ERR_NOT_CONVERGED, DAWN_ERR_TIMEOUT, DAWN_ERR_BOUNDS = 4, 5, 6
 DAWN_OPT_MAX_STEPS, DAWN_OPT_WAIT_LIMIT_NS, DAWN_OPT_GRID_BLOCKS, DAWN_OPT_TEST_STALL = 1, 2, 3, 4
 DAWN_OPT_TRACE_STEPS = 5
 DAWN_OPT_GSVM = 6
+DAWN_OPT_CTAS_PER_SM, DAWN_OPT_BATCH = 7, 8
+DAWN_TUNE_SSSP, DAWN_TUNE_MSSSP, DAWN_TUNE_ROOTS = 0, 1, 2
 
 EXPORTS = ("dawn_create_graph", "dawn_set_weights", "dawn_reserve", "dawn_sssp", "dawn_msssp", "dawn_sssp_roots",
            "dawn_sssp_backward", "dawn_status", "dawn_get_stats", "dawn_set_option", "dawn_get_trace", "dawn_graph_info",
-           "dawn_status_string", "dawn_destroy", "dawn_sssp_noalloc")
+           "dawn_status_string", "dawn_destroy", "dawn_sssp_noalloc", "dawn_autotune")
 
 
 class DawnError(RuntimeError):
@@ -41,6 +43,11 @@ class DawnError(RuntimeError):
 
 class _Stats(ctypes.Structure):
     _fields_ = [(f, ctypes.c_int64) for f in ("steps", "frontier_sum", "edges_scanned", "updates", "instances")]
+
+
+class _Tuning(ctypes.Structure):
+    _fields_ = [("ctas_per_sm", ctypes.c_int32), ("grid_blocks", ctypes.c_int32), ("batch", ctypes.c_int32),
+                ("candidates", ctypes.c_int32), ("best_ms", ctypes.c_float), ("default_ms", ctypes.c_float)]
 
 
 _lib = None
@@ -71,6 +78,7 @@ def load_library(path: str = LIB_PATH):
         "dawn_status_string": ([c_int], ctypes.c_char_p),
         "dawn_destroy": ([vp], None),
         "dawn_sssp_noalloc": ([vp, i32, vp, vp, vp, vp, vp], c_int),
+        "dawn_autotune": ([vp, c_int, vp, i32, i32, vp, ctypes.POINTER(_Tuning)], c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -199,6 +207,19 @@ def dawn_set_option(g: int, option: int, value: int):
     _check(load_library().dawn_set_option(ctypes.c_void_p(g), int(option), int(value)), "dawn_set_option")
 
 
+def dawn_autotune(g: int, mode: int, sources, reps: int = 3, stream=None) -> dict:
+    """Time candidate launch configurations on `sources` (host int32 ids) and
+    keep the fastest as the handle's options; returns the chosen
+    configuration and its timing.  Synchronous."""
+    import numpy as np
+    src = np.ascontiguousarray(np.asarray(sources, dtype=np.int32))
+    tun = _Tuning()
+    _check(load_library().dawn_autotune(ctypes.c_void_p(g), int(mode), ctypes.c_void_p(src.ctypes.data),
+                                        int(src.size), int(reps), _stream(stream), ctypes.byref(tun)),
+           "dawn_autotune")
+    return {f: getattr(tun, f) for f, _ in _Tuning._fields_}
+
+
 def dawn_get_trace(g: int, cap: int = 4096):
     """Per-step rows of the last solve: list of (t_ns, frontier, edges) per
     step, derived from the cumulative device trace."""
@@ -297,6 +318,14 @@ class Graph:
 
     def set_option(self, option: int, value: int):
         dawn_set_option(self.handle, option, value)
+
+    def autotune(self, sources, mode: str = "sssp", reps: int = 3, stream=None) -> dict:
+        """Pick and keep the fastest launch configuration for `sources`
+        (mode "sssp": one dawn_sssp per source; "msssp": one batched solve;
+        "roots": one multi-root solve)."""
+        m = {"sssp": DAWN_TUNE_SSSP, "msssp": DAWN_TUNE_MSSSP, "roots": DAWN_TUNE_ROOTS}[mode]
+        with torch.cuda.device(self.device):
+            return dawn_autotune(self.handle, m, sources, reps, stream)
 
 
 class DawnSSSP(torch.autograd.Function):
