@@ -65,9 +65,10 @@ typedef enum {
   DAWN_ERR_BOUNDS = 6         /* an internal capacity check failed; the kernel returned */
 } dawn_status_code;
 
-/* Per-solve counters summed over all instances of the last solve. */
+/* Counters of the last solve call, summed over all its instances (a batched
+ * call split into several launches sums all of them). */
 typedef struct {
-  int64_t steps;         /* GOVM steps executed (frontier non-empty) */
+  int64_t steps;         /* GOVM steps executed (frontier non-empty); the most of any launch */
   int64_t frontier_sum;  /* sum over steps of |delta| (frontier vertices, out-degree >= 1) */
   int64_t edges_scanned; /* sum over steps of the frontier's out-edges (edges relaxed) */
   int64_t updates;       /* path updates: vertices whose distance strictly dropped in a step
@@ -104,8 +105,18 @@ int dawn_create_graph(int32_t n, int64_t m, const int32_t *row_ptr, const int32_
 /*
  * Replace the edge weights (same type and count as at creation), e.g. after
  * a gradient step.  Same validation and ownership rules as creation.
+ *   flags  DAWN_WEIGHTS_ON_DEVICE: `weights` is device memory (else host);
+ *          DAWN_WEIGHTS_DEFER_CHECK: do not wait for the validation result.
+ *          The call then returns DAWN_OK without synchronising, and a later
+ *          solve on the handle refuses invalid weights itself: it writes no
+ *          output and reports DAWN_ERR_INVALID in dawn_status (stream
+ *          ordered: issue the solve on the same stream, or order the streams).
+ * Every solve checks the verdict of the weights in force, so weights that a
+ * synchronous call rejected (the copy has already replaced the old ones) are
+ * refused as well until valid weights are set.
  */
-int dawn_set_weights(dawn_graph g, const void *weights, int inputs_on_device, void *stream);
+enum { DAWN_WEIGHTS_ON_DEVICE = 1, DAWN_WEIGHTS_DEFER_CHECK = 2 };
+int dawn_set_weights(dawn_graph g, const void *weights, int flags, void *stream);
 
 /*
  * Pre-size the solver workspace for batches of up to k instances (optional;

@@ -228,8 +228,22 @@ int grid_for(dawn_graph g, int32_t k) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(cap, want));
 }
 
+// Largest n * max|w| the weight type allows; 0 = no bound.
+uint32_t weight_limit(int wtype) {
+  // uint32: every candidate dist(u) + w is at most n * max(w) (shortest paths
+  // are simple); it must stay below the unreachable sentinel.
+  if (wtype == DAWN_W_U32) return 0xFFFFFFFFu;
+  // int32: every simple-path sum and candidate lies in [-n max|w|, n max|w|],
+  // which must stay inside int32 and below the unreachable sentinel INT32_MAX
+  if (wtype == DAWN_W_I32) return 0x7FFFFFFFu;
+  return 0;
+}
+
+// One persistent launch.  `accumulate` (later launches of one batched call)
+// keeps the status and the counters of the earlier launches: only the
+// barrier word and the per-step change flags start again from zero.
 int run_solve(dawn_graph g, const int32_t *seeds, int32_t nseeds, int32_t source, int32_t k, int roots_mode,
-              void *dist, int32_t *parent, int32_t *parent_edge, cudaStream_t stream) {
+              void *dist, int32_t *parent, int32_t *parent_edge, cudaStream_t stream, bool accumulate = false) {
   int rc = ensure_workspace(g, k);
   if (rc) return rc;
   GovmParams p = {};
@@ -260,7 +274,15 @@ int run_solve(dawn_graph g, const int32_t *seeds, int32_t nseeds, int32_t source
   p.gsvm = g->gsvm;
   p.trace = g->trace;
   p.trace_cap = g->trace_cap;
-  cudaError_t e = cudaMemsetAsync(g->ctl, 0, sizeof(DeviceCtl), stream);
+  p.vflags = g->vflags;
+  p.vlimit = weight_limit(g->wtype);
+  cudaError_t e;
+  if (accumulate) {
+    e = cudaMemsetAsync(&g->ctl->bar, 0, sizeof(g->ctl->bar), stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g->ctl->changed, 0, sizeof(g->ctl->changed), stream);
+  } else {
+    e = cudaMemsetAsync(g->ctl, 0, sizeof(DeviceCtl), stream);
+  }
   if (e == cudaSuccess && g->trace)
     e = cudaMemsetAsync(g->trace, 0, (size_t)g->trace_cap * 4 * sizeof(unsigned long long), stream);
   if (e != cudaSuccess) return cuda_fail(e);
@@ -282,7 +304,9 @@ int copy_in(void *dst, const void *src, size_t bytes, int on_device, cudaStream_
 }
 
 // Validates the device copy of the graph; synchronous.
-int validate(dawn_graph g, cudaStream_t stream) {
+// Runs the validation kernel; with `wait` the verdict is read back and
+// returned, otherwise only the next solve sees it (through GovmParams).
+int validate(dawn_graph g, cudaStream_t stream, bool wait = true) {
   cudaError_t e = cudaMemsetAsync(g->vflags, 0, 2 * sizeof(unsigned), stream);
   if (e != cudaSuccess) return cuda_fail(e);
   const int64_t work = std::max<int64_t>(g->m, (int64_t)g->n + 1);
@@ -291,16 +315,14 @@ int validate(dawn_graph g, cudaStream_t stream) {
                                                g->vflags);
   unsigned h[2] = {0, 0};
   e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e);
+  if (!wait) return DAWN_OK;
   if (e == cudaSuccess) e = cudaMemcpyAsync(h, g->vflags, sizeof(h), cudaMemcpyDeviceToHost, stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
   if (e != cudaSuccess) return cuda_fail(e);
   if (h[0]) return DAWN_ERR_INVALID;
-  // uint32: every candidate dist(u) + w is at most n * max(w) (shortest paths
-  // are simple); it must stay below the unreachable sentinel.
-  if (g->wtype == DAWN_W_U32 && (uint64_t)g->n * (uint64_t)h[1] >= 0xFFFFFFFFull) return DAWN_ERR_INVALID;
-  // int32: every simple-path sum and candidate lies in [-n max|w|, n max|w|],
-  // which must stay inside int32 and below the unreachable sentinel INT32_MAX
-  if (g->wtype == DAWN_W_I32 && (uint64_t)g->n * (uint64_t)h[1] >= 0x7FFFFFFFull) return DAWN_ERR_INVALID;
+  const uint32_t lim = weight_limit(g->wtype);
+  if (lim && (uint64_t)g->n * (uint64_t)h[1] >= lim) return DAWN_ERR_INVALID;
   return DAWN_OK;
 }
 
@@ -396,14 +418,15 @@ int dawn_create_graph(int32_t n, int64_t m, const int32_t *row_ptr, const int32_
   return DAWN_OK;
 }
 
-int dawn_set_weights(dawn_graph g, const void *weights, int inputs_on_device, void *stream) {
-  if (!g || (g->m > 0 && !weights)) return DAWN_ERR_INVALID;
+int dawn_set_weights(dawn_graph g, const void *weights, int flags, void *stream) {
+  if (!g || (g->m > 0 && !weights) || (flags & ~(DAWN_WEIGHTS_ON_DEVICE | DAWN_WEIGHTS_DEFER_CHECK)))
+    return DAWN_ERR_INVALID;
   if (set_device(g)) return DAWN_ERR_CUDA;
   cudaStream_t s = (cudaStream_t)stream;
-  int rc = copy_in(g->w, weights, (size_t)g->m * 4, inputs_on_device, s);
+  int rc = copy_in(g->w, weights, (size_t)g->m * 4, flags & DAWN_WEIGHTS_ON_DEVICE, s);
   if (rc) return rc;
   g->last_stream = s;
-  if ((rc = validate(g, s))) return rc;
+  if ((rc = validate(g, s, !(flags & DAWN_WEIGHTS_DEFER_CHECK)))) return rc;
   if (g->m > 0) {
     const int eb = (int)std::max<int64_t>(1, std::min<int64_t>((g->m + 255) / 256, (int64_t)g->sms * 16));
     interleave_kernel<<<eb, 256, 0, s>>>(nullptr, g->w, g->m, g->cw);
@@ -436,7 +459,7 @@ int dawn_msssp(dawn_graph g, const int32_t *sources, int32_t k, void *dist, int3
     const int32_t kk = std::min(chunk, k - b);
     const size_t off = (size_t)b * g->n;
     int rc = run_solve(g, sources + b, kk, 0, kk, 0, (uint32_t *)dist + off, parent ? parent + off : nullptr,
-                       nullptr, (cudaStream_t)stream);
+                       nullptr, (cudaStream_t)stream, b > 0);
     if (rc) return rc;
   }
   return DAWN_OK;
@@ -659,6 +682,8 @@ extern "C" int dawn_sssp_noalloc(dawn_graph g, int32_t source, void *dist, int32
   p.test_stall = 0;
   p.trace = nullptr;
   p.trace_cap = 0;
+  p.vflags = g->vflags;
+  p.vlimit = weight_limit(g->wtype);
   // the control block (barrier counters, status) must start at zero; the
   // kernel itself resets everything else it reads
   cudaError_t e = cudaMemsetAsync(ctl, 0, sizeof(DeviceCtl), s);

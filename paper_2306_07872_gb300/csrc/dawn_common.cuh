@@ -83,6 +83,12 @@ struct GovmParams {
   int gsvm;                  // 1: run Algorithm 1 (rescan every reached vertex each step)
   unsigned long long *trace;  // optional per-step trace [trace_cap][4], null when off
   int32_t trace_cap;
+  // Validation verdict of the graph's current weights (written by the
+  // validation kernel): [0] error bits, [1] largest |w|.  A solve refuses to
+  // run (DAWN_ERR_INVALID) when an error bit is set or n * max|w| reaches
+  // vlimit (0: no bound).  This makes deferred validation stream-ordered.
+  const unsigned *vflags;
+  uint32_t vlimit;
 };
 
 // Host-side launchers (govm_kernel.cu).

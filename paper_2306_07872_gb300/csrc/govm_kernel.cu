@@ -230,8 +230,8 @@ __device__ __forceinline__ int32_t find_instance(const int32_t *tprefix, int32_t
 }
 
 // Build delta (queue + tile table + tails_next) from beta (the bitmap) for
-// every instance; consumes (clears) the bitmap.  Work is split into 32-word
-// chunks (1024 vertices) handed to warps round-robin; a warp ranks the marked
+// every instance; consumes (clears) the bitmap.  Work is split into chunks
+// of up to 32 words (1024 vertices) handed to warps round-robin; a warp ranks the marked
 // vertices of its chunk with a popcount scan and expands them in rounds of
 // 128 (four consecutive ranks per lane), so all row_ptr reads of a round are
 // in flight together and no block-wide synchronisation is needed.  One
@@ -245,16 +245,22 @@ __device__ void build_frontier(const GovmParams &p, unsigned long long *tails_ne
   const int lane = threadIdx.x & 31;
   const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const int64_t cpi = (p.words + 31) / 32;  // 32-word chunks per instance
+  // Chunks of 32 words (1024 vertices); a bitmap too small to give every
+  // other warp a chunk (a small graph, one block) is cut into narrower
+  // chunks so that more warps share the build.
+  int64_t cwd = 32;
+  if ((p.words * p.k + 31) / 32 * 2 < nwarps)
+    cwd = max((int64_t)1, min((int64_t)32, (p.words * p.k + nwarps - 1) / nwarps));
+  const int64_t cpi = (p.words + cwd - 1) / cwd;  // chunks per instance
   const int64_t chunks = cpi * p.k;
   uint32_t *wbits = wt.ebase;  // the relax tile buffers are free during the build
   uint32_t *wstart = wt.dkey;
   for (int64_t ch = gwarp; ch < chunks; ch += nwarps) {
     const int32_t inst = (int32_t)(ch / cpi);
-    const int64_t w0 = (ch - (int64_t)inst * cpi) * 32;
+    const int64_t w0 = (ch - (int64_t)inst * cpi) * cwd;
     uint32_t *bm = p.bitmap + (size_t)inst * p.words;
     uint32_t bits = 0;
-    if (w0 + lane < p.words) {
+    if (lane < cwd && w0 + lane < p.words) {
       bits = __ldcg(bm + w0 + lane);
       if (bits && !p.gsvm) bm[w0 + lane] = 0u;  // Algorithm 1 keeps every reached vertex
     }
@@ -543,6 +549,13 @@ __global__ void __launch_bounds__(kBlockThreads, MINB) govm_kernel(GovmParams p)
     }
   }
 
+  // Weights refused by validation (possibly deferred, see dawn_set_weights)
+  // stop the solve before its first barrier, with no output written.
+  if (p.vflags && blockIdx.x == 0 && tid == 0) {
+    const unsigned bad = __ldcg(p.vflags), wmax = __ldcg(p.vflags + 1);
+    if (bad || (p.vlimit && (unsigned long long)p.n * wmax >= p.vlimit)) set_status(ctl, DAWN_ERR_INVALID);
+  }
+
   // 1. alpha = +inf, beta = {}.
   for (int32_t i = 0; i < p.k; ++i) {
     unsigned long long *st = p.state + (size_t)i * p.n;
@@ -656,7 +669,7 @@ finish:
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) u += __shfl_down_sync(kFull, u, d);
     if (lane == 0 && u) atomicAdd(&ctl->updates, u);
-    if (gtid == 0) ctl->steps = (unsigned long long)step;
+    if (gtid == 0) atomicMax(&ctl->steps, (unsigned long long)step);  // batched calls: the longest launch
   }
 }
 

@@ -29,6 +29,7 @@ DAWN_OPT_TRACE_STEPS = 5
 DAWN_OPT_GSVM = 6
 DAWN_OPT_CTAS_PER_SM, DAWN_OPT_BATCH = 7, 8
 DAWN_TUNE_SSSP, DAWN_TUNE_MSSSP, DAWN_TUNE_ROOTS = 0, 1, 2
+DAWN_WEIGHTS_ON_DEVICE, DAWN_WEIGHTS_DEFER_CHECK = 1, 2
 
 EXPORTS = ("dawn_create_graph", "dawn_set_weights", "dawn_reserve", "dawn_sssp", "dawn_msssp", "dawn_sssp_roots",
            "dawn_sssp_backward", "dawn_status", "dawn_get_stats", "dawn_set_option", "dawn_get_trace", "dawn_graph_info",
@@ -147,9 +148,10 @@ def dawn_create_graph(row_ptr: torch.Tensor, col_idx: torch.Tensor, weights: tor
     return h.value
 
 
-def dawn_set_weights(g: int, weights: torch.Tensor, stream=None):
+def dawn_set_weights(g: int, weights: torch.Tensor, stream=None, defer_check: bool = False):
     w, on_dev = _any(weights, weights.dtype, "weights")
-    _check(load_library().dawn_set_weights(ctypes.c_void_p(g), w, on_dev, _stream(stream)), "dawn_set_weights")
+    flags = (DAWN_WEIGHTS_ON_DEVICE if on_dev else 0) | (DAWN_WEIGHTS_DEFER_CHECK if defer_check else 0)
+    _check(load_library().dawn_set_weights(ctypes.c_void_p(g), w, flags, _stream(stream)), "dawn_set_weights")
 
 
 def dawn_reserve(g: int, k: int):
@@ -329,20 +331,23 @@ class Graph:
 
 
 class DawnSSSP(torch.autograd.Function):
-    """dist = DawnSSSP.apply(weights, graph, source).
+    """dist = DawnSSSP.apply(weights, graph, source, check=True).
 
     Forward: loads `weights` (float32, one per CSR edge) into the graph and
-    runs the GOVM solver, saving only the parent tree.  Backward: the
-    library's kernel scatters dL/ddist along the parent tree, giving dL/dw
-    (the sum of dL/ddist over the subtree below each tree edge, 0 off the
-    tree)."""
+    runs the GOVM solver, saving only the parent tree.  The weights are
+    validated in stream order (the solve itself refuses invalid weights);
+    with check=True the forward waits once for the solve's status and raises
+    DawnError on any failure, with check=False it never synchronises and the
+    caller reads the status later (Graph.check).  Backward: the library's
+    kernel scatters dL/ddist along the parent tree, giving dL/dw (the sum of
+    dL/ddist over the subtree below each tree edge, 0 off the tree)."""
 
     @staticmethod
-    def forward(ctx, weights: torch.Tensor, graph: Graph, source: int):
+    def forward(ctx, weights: torch.Tensor, graph: Graph, source: int, check: bool = True):
         if weights.dtype != torch.float32 or graph.wtype != DAWN_W_F32:
             raise TypeError("DawnSSSP needs a float32 graph and float32 weights")
-        dawn_set_weights(graph.handle, weights.detach().contiguous())
-        dist, _, pe = graph.sssp(source, parent=False, parent_edge=True)
+        dawn_set_weights(graph.handle, weights.detach().contiguous(), defer_check=True)
+        dist, _, pe = graph.sssp(source, parent=False, parent_edge=True, check=check)
         ctx.graph = graph
         ctx.save_for_backward(pe)
         ctx.mark_non_differentiable(pe)
@@ -354,4 +359,4 @@ class DawnSSSP(torch.autograd.Function):
         g = ctx.graph
         grad_w = torch.empty(g.m, dtype=torch.float32, device=grad_dist.device)
         dawn_sssp_backward(g.handle, pe, grad_dist.contiguous().float(), grad_w)
-        return grad_w, None, None
+        return grad_w, None, None, None

@@ -125,3 +125,19 @@ def test_autotune_rejects_bad_input(dawn):
             dawn.dawn_autotune(g.handle, mode, np.array(src, np.int32))
         assert e.value.code == dawn.DAWN_ERR_INVALID
     exact(g, wl.row_ptr, wl.col, wl.weights, wl.sources[0])
+
+
+def test_batched_counters_cover_every_launch(dawn):
+    # a call split into several launches reports counters summed over all of them
+    wl = gg.rmat_u32(12, 8, nsrc=40, seed=29)
+    g = dawn.Graph(wl.row_ptr, wl.col, wl.weights)
+    per = {}
+    for batch in (0, 5):
+        g.set_option(dawn.DAWN_OPT_BATCH, batch)
+        g.msssp(wl.sources, parent=False)
+        st = g.stats()
+        assert st["instances"] == 40 and st["steps"] >= 1
+        per[batch] = st
+    for key in ("edges_scanned", "updates", "frontier_sum"):
+        ratio = per[5][key] / per[0][key]
+        assert 0.8 < ratio < 1.25, (key, per)
