@@ -23,6 +23,8 @@
 // No host round trip happens between steps.
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include "dawn_common.cuh"
 
 namespace dawn {
@@ -673,7 +675,8 @@ finish:
   }
 }
 
-// Shared memory exceeds the 48 KB static limit: opt in once per kernel.
+// The block's shared memory is dynamic; the opt-in to sizes above 48 KB is
+// set once per kernel and device, so that kTile may grow without a change here.
 using GovmFn = void (*)(GovmParams);
 
 template <int MINB>
@@ -688,15 +691,19 @@ GovmFn kernel_for(int wtype, int ctas_per_sm) {
 }
 
 cudaError_t prepare_kernels() {
-  static bool done = false;
-  if (done) return cudaSuccess;
-  cudaError_t e = cudaSuccess;
+  // function attributes are per device: remember which devices are done
+  static std::atomic<unsigned long long> done{0};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = 1ull << (dev & 63);
+  if (done.load() & bit) return cudaSuccess;
   for (int wtype : {DAWN_W_U32, DAWN_W_F32, DAWN_W_I32})
     for (int c : {4, 5})
       if (e == cudaSuccess)
         e = cudaFuncSetAttribute(kernel_for(wtype, c), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)sizeof(BlockShared));
-  done = e == cudaSuccess;
+  if (e == cudaSuccess) done.fetch_or(bit);
   return e;
 }
 
