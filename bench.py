@@ -222,6 +222,7 @@ def run_sssp_bench(args, wl, device, world, rank):
         torch.cuda.synchronize()
     barrier(world)
     g.check()
+    dist_host = dist.cpu().numpy() if (rank == 0 and not args.no_cpu) else None
     elapsed = t0.elapsed_time(t1) / 1e3
     elapsed = max_over_ranks(elapsed, world)
     launch_ms = np.array([[a.elapsed_time(b) for a, b in row] for row in evs])  # [K, S]
@@ -231,6 +232,7 @@ def run_sssp_bench(args, wl, device, world, rank):
     achieved_gbs_total = float(b_alg.sum() / (per_src_ms.sum() / 1e3) / 1e9)
     mu = float(np.mean([st["updates"] for st in stats]))
     res = {
+        "dist_host": dist_host,
         "tuning": tuning,
         "elapsed": elapsed,
         "gteps": S * args.steps * world * wl.e_wcc / elapsed / 1e9,
@@ -316,22 +318,34 @@ def run_e2e(args, wl, device, world, tuning=None):
             "d2h_bytes_per_step": int(d2h), "steps": steps, "ms_per_step": el / steps * 1e3}
 
 
-def cpu_baseline(wl, budget_s: float = 20.0):
+def cpu_baseline(wl, budget_s: float = 20.0, gpu_dist=None):
     """The oracle's literal GOVM iteration (Algorithm 2) on the host cores,
-    one source per thread, on a bounded sample of the sources."""
+    one source per thread, on a bounded sample of the sources; plus the
+    single-core time of one source by Algorithm 2 and by Dijkstra.  With
+    `gpu_dist` (row i = the GPU's distances from source i) every sampled
+    source is also compared bit for bit with the GPU."""
     import oracle
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
     threads = max(1, min(cores, 16, len(wl.sources)))
     # one probe solve sizes the sample to the time budget
     t, _ = oracle.timed_govm(wl.row_ptr, wl.col, wl.weights, [int(wl.sources[0])], threads=1)
+    t0 = time.perf_counter()
+    oracle.dijkstra(wl.row_ptr, wl.col, wl.weights, int(wl.sources[0]))
+    t_dij = time.perf_counter() - t0
     rounds = max(1, int(budget_s / max(t, 1e-3) / 2))
     nsrc = min(len(wl.sources), threads * rounds)
     sample = [int(s) for s in wl.sources[:nsrc]]
     el, res = oracle.timed_govm(wl.row_ptr, wl.col, wl.weights, sample, threads=threads)
-    return {"value": len(sample) * wl.e_wcc / el / 1e9, "unit": "GTEPS", "cores": threads, "kind": "oracle",
-            "sample": f"{len(sample)} of the {len(wl.sources)} sources, literal GOVM (Algorithm 2), "
-                      f"one source per thread, {threads} threads, {el:.1f} s",
-            "mu_oracle": float(np.mean([r[1]["mu"] for r in res]))}
+    out = {"value": len(sample) * wl.e_wcc / el / 1e9, "unit": "GTEPS", "cores": threads, "kind": "oracle",
+           "sample": f"{len(sample)} of the {len(wl.sources)} sources, literal GOVM (Algorithm 2), "
+                     f"one source per thread, {threads} threads, {el:.1f} s",
+           "mu_oracle": float(np.mean([r[1]["mu"] for r in res])),
+           "single_core_ms_per_source": {"govm_alg2": t * 1e3, "dijkstra": t_dij * 1e3}}
+    if gpu_dist is not None:
+        same = [np.array_equal(np.asarray(r[0]).view(np.uint32), gpu_dist[i].view(np.uint32))
+                for i, r in enumerate(res)]
+        out["bit_exact_vs_gpu"] = {"sources_compared": len(same), "all_equal": bool(all(same))}
+    return out
 
 
 # ------------------------------------------------- batched and differentiable
@@ -641,7 +655,7 @@ def main_ours(args):
         log(f"[bench] device: {res['gteps']:.2f} GTEPS, {res['launch_ms_mean']:.3f} ms/launch, "
             f"B_alg {res['b_alg_mean'] / 1e9:.3f} GB, {res['achieved_gbs']:.0f} GB/s, steps {res['steps_mean']:.1f}")
         e2e = run_e2e(args, wl, device, world, res["tuning"]) if not args.no_e2e else None
-        cpu = cpu_baseline(wl, args.cpu_budget) if (rank == 0 and not args.no_cpu) else None
+        cpu = cpu_baseline(wl, args.cpu_budget, res["dist_host"]) if (rank == 0 and not args.no_cpu) else None
         if rank != 0:
             return
         peak, peak_kind = measured_peak()
