@@ -53,7 +53,7 @@ def measured_peak():
 
 
 KERNEL_SOURCES = ("paper_2306_07872_gb300/csrc/govm_kernel.cu", "paper_2306_07872_gb300/csrc/dawn_common.cuh")
-TRAFFIC_SUMMARY = "profiles/govm_kernel_rmat22_traffic.md"
+TRAFFIC_SUMMARIES = "profiles/govm_kernel_*_traffic.md"
 
 
 def kernel_hash() -> str:
@@ -66,21 +66,24 @@ def kernel_hash() -> str:
 
 
 def recorded_traffic(workload: str):
-    """Per-launch DRAM bytes of govm_kernel from the committed ncu summary,
-    or None when the summary is missing, is for another workload, or was taken
-    on a different version of the kernel sources."""
-    try:
-        with open(os.path.join(ROOT, TRAFFIC_SUMMARY)) as f:
-            kv = dict(l.split(":", 1) for l in f.read().splitlines() if l.startswith("- ") and ":" in l)
-    except OSError:
-        return None
-    kv = {k[2:].strip(): v.strip().strip("`") for k, v in kv.items()}
-    if kv.get("kernel_source_sha256_16") != kernel_hash() or kv.get("workload") != workload:
-        return None
-    try:
-        return float(kv["dram_bytes_per_launch"])
-    except (KeyError, ValueError):
-        return None
+    """Per-launch DRAM bytes of govm_kernel from the committed ncu summary of
+    this workload, or None when there is none or it was taken on a different
+    version of the kernel sources."""
+    import glob
+    for path in sorted(glob.glob(os.path.join(ROOT, TRAFFIC_SUMMARIES))):
+        try:
+            with open(path) as f:
+                kv = dict(l.split(":", 1) for l in f.read().splitlines() if l.startswith("- ") and ":" in l)
+        except OSError:
+            continue
+        kv = {k[2:].strip(): v.strip().strip("`") for k, v in kv.items()}
+        if kv.get("workload") != workload or kv.get("kernel_source_sha256_16") != kernel_hash():
+            continue
+        try:
+            return float(kv["dram_bytes_per_launch"])
+        except (KeyError, ValueError):
+            return None
+    return None
 
 
 def dist_env():
