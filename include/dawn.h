@@ -174,8 +174,14 @@ int dawn_sssp_roots(dawn_graph g, const int32_t *roots, int32_t k, void *dist, i
  *   grad_dist    device float32[n] (dL/ddist; entries of unreachable
  *                vertices are ignored)
  *   grad_w       device float32[m], overwritten
- * A parent_edge array that contains a cycle makes the call fail with
- * DAWN_ERR_INVALID in dawn_status().
+ * The tree is processed children before parents (reverse tree order, the
+ * reverse of distance order for positive weights): O(n + m) work whatever the
+ * number of non-zero dL/ddist entries.  The sums run in float32 in an order
+ * that varies from call to call, so the last bits may differ between calls.
+ * A parent_edge array that contains a cycle or an edge index outside [0, m)
+ * makes the call fail with DAWN_ERR_INVALID in dawn_status().  The first call
+ * on a handle allocates 16 bytes per vertex of scratch (make one call before
+ * capturing the backward into a CUDA graph).
  */
 int dawn_sssp_backward(dawn_graph g, const int32_t *parent_edge, const float *grad_dist, float *grad_w,
                        void *stream);

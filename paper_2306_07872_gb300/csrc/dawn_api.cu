@@ -37,6 +37,10 @@ struct dawn_graph_s {
   int64_t words = 0, tiles_cap = 0;
   DeviceCtl *ctl = nullptr;
   unsigned *vflags = nullptr;  // validation flags [0] and max weight [1]
+  // backward scratch (allocated by the first dawn_sssp_backward)
+  float *bw_acc = nullptr;        // [n] subtree sums of dL/ddist
+  int32_t *bw_cnt = nullptr;      // [3n] has-children flags, children still to arrive, tree parents
+  unsigned long long *bw_edges = nullptr;  // [3] tree edges expected, handled; blocks finished
   // options
   int64_t max_steps = 0;
   unsigned long long wait_limit_ns = 4000000000ull;
@@ -112,37 +116,85 @@ __global__ void interleave_kernel(const int32_t *col, const uint32_t *w, int64_t
   }
 }
 
-__global__ void zero_f32_kernel(float *p, int64_t count) {
-  const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long gsize = (long long)gridDim.x * blockDim.x;
-  for (long long i = gtid; i < count; i += gsize) p[i] = 0.0f;
+// Backward of dist w.r.t. the weights along the parent tree, children before
+// parents: acc[v] starts at dL/ddist[v]; once every tree child of v has added
+// its acc, acc[v] is the sum of dL/ddist over v's subtree, grad_w of v's
+// parent edge is set to it and it is added to the parent.  A thread starts at
+// each leaf and walks up, going through a parent only as the last of its
+// children to arrive, so every tree edge is handled once (O(n) work, no
+// barrier).  Edges off the tree keep grad_w = 0.  A parent array with a cycle
+// leaves the cycle's edges unhandled, which the final check reports.
+
+__device__ __forceinline__ int atom_add_acq_rel_s32(int *p, int v) {
+  int o;
+  asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], %2;" : "=r"(o) : "l"(p), "r"(v) : "memory");
+  return o;
 }
 
-// Backward of dist w.r.t. the weights along the parent tree: every vertex v
-// with a non-zero dL/ddist[v] adds it to each tree edge on its path to the
-// root, so grad_w[e] ends up as the sum of dL/ddist over the subtree below e.
-// A walk longer than n edges means the parent array has a cycle.
-__global__ void backward_walk_kernel(const int32_t *parent_edge, const float *grad_dist, const int32_t *src,
-                                     float *grad_w, int32_t n, int64_t m, DeviceCtl *ctl) {
+// acc = dL/ddist; par[v] = tree parent of v (or -1); rem[u] = number of tree
+// children of u and inner[u] = 1 when there is one (both start at zero);
+// edges[0] = tree edges; grad_w = 0 (the walk writes the tree edges after
+// this kernel).
+__global__ void bw_count_kernel(const int32_t *parent_edge, const float *grad_dist, const int32_t *src, int32_t n,
+                                int64_t m, float *acc, int32_t *inner, int32_t *rem, int32_t *par,
+                                unsigned long long *edges, float *grad_w, DeviceCtl *ctl) {
   const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long gsize = (long long)gridDim.x * blockDim.x;
+  for (long long e = gtid; e < m; e += gsize) grad_w[e] = 0.0f;
+  unsigned long long mine = 0;
   for (long long v = gtid; v < n; v += gsize) {
-    const float g = grad_dist[v];
-    int32_t e = parent_edge[v];
-    if (g == 0.0f || e < 0) continue;
-    int32_t hops = 0;
-    while (e >= 0) {
-      if ((int64_t)e >= m) {
-        atomicCAS(&ctl->status, 0, (int)DAWN_ERR_INVALID);
-        break;
-      }
-      atomicAdd(grad_w + e, g);
-      const int32_t u = src[e];
-      e = parent_edge[u];
-      if (++hops > n) {
-        atomicCAS(&ctl->status, 0, (int)DAWN_ERR_INVALID);
-        break;
-      }
+    acc[v] = grad_dist[v];
+    const int32_t e = parent_edge[v];
+    par[v] = -1;
+    if (e < 0) continue;
+    if ((int64_t)e >= m) {
+      atomicCAS(&ctl->status, 0, (int)DAWN_ERR_INVALID);
+      continue;
+    }
+    const int32_t u = src[e];
+    par[v] = u;
+    inner[u] = 1;  // a plain store: every child writes the same value
+    atomicAdd(rem + u, 1);
+    ++mine;
+  }
+  for (int d = 16; d > 0; d >>= 1) mine += __shfl_xor_sync(0xFFFFFFFFu, mine, d);
+  if ((threadIdx.x & 31) == 0 && mine) atomicAdd(edges, mine);
+}
+
+// The walks; the last block to finish checks that every tree edge was
+// handled once (otherwise the parent array had a cycle).
+__global__ void bw_walk_kernel(const int32_t *parent_edge, const int32_t *par, int32_t n, float *acc,
+                               const int32_t *inner, int32_t *rem, float *grad_w, unsigned long long *edges,
+                               DeviceCtl *ctl) {
+  const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long gsize = (long long)gridDim.x * blockDim.x;
+  unsigned long long mine = 0;
+  for (long long v = gtid; v < n; v += gsize) {
+    if (inner[v] != 0) continue;  // walks start at leaves only
+    int32_t x = (int32_t)v;
+    for (int32_t hop = 0; hop < n; ++hop) {  // a tree path has fewer than n edges
+      const int32_t u = par[x];            // -1: a root, or an edge index the count rejected
+      const int32_t e = parent_edge[x];
+      const float sum = __ldcg(acc + x);  // complete: every child of x has added to it
+      if (u < 0) break;
+      grad_w[e] = sum;
+      ++mine;
+      atomicAdd(acc + u, sum);
+      // release: the add above is visible to the sibling that arrives last;
+      // acquire: as the last, every sibling's add is visible below
+      if (atom_add_acq_rel_s32(rem + u, -1) != 1) break;
+      x = u;
+    }
+  }
+  for (int d = 16; d > 0; d >>= 1) mine += __shfl_xor_sync(0xFFFFFFFFu, mine, d);
+  if ((threadIdx.x & 31) == 0 && mine) atomicAdd(edges + 1, mine);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned long long done = atomicAdd(edges + 2, 1ull);
+    if (done == gridDim.x - 1) {  // last block: all walks have finished
+      __threadfence();
+      if (__ldcg(edges) != __ldcg(edges + 1)) atomicCAS(&ctl->status, 0, (int)DAWN_ERR_INVALID);
     }
   }
 }
@@ -336,6 +388,9 @@ void release(dawn_graph g) {
   cudaFree(g->src);
   cudaFree(g->ctl);
   cudaFree(g->vflags);
+  cudaFree(g->bw_acc);
+  cudaFree(g->bw_cnt);
+  cudaFree(g->bw_edges);
   delete g;
 }
 
@@ -478,13 +533,30 @@ int dawn_sssp_backward(dawn_graph g, const int32_t *parent_edge, const float *gr
   if (g->wtype != DAWN_W_F32) return DAWN_ERR_INVALID;
   if (set_device(g)) return DAWN_ERR_CUDA;
   cudaStream_t s = (cudaStream_t)stream;
+  if (!g->bw_acc) {
+    int rc;
+    if ((rc = dalloc(&g->bw_acc, (size_t)g->n)) || (rc = dalloc(&g->bw_cnt, 3 * (size_t)g->n)) ||
+        (rc = dalloc(&g->bw_edges, 3))) {
+      cudaFree(g->bw_acc);
+      cudaFree(g->bw_cnt);
+      g->bw_acc = nullptr;
+      g->bw_cnt = nullptr;
+      return rc;
+    }
+  }
   cudaError_t e = cudaMemsetAsync(g->ctl, 0, sizeof(DeviceCtl), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(g->bw_cnt, 0, 2 * sizeof(int32_t) * (size_t)g->n, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(g->bw_edges, 0, 3 * sizeof(unsigned long long), s);
   if (e != cudaSuccess) return cuda_fail(e);
   if (g->m > 0) {
-    const int zb = (int)std::max<int64_t>(1, std::min<int64_t>((g->m + 255) / 256, (int64_t)g->sms * 8));
-    zero_f32_kernel<<<zb, 256, 0, s>>>(grad_w, g->m);
-    const int wb = (int)std::max<int64_t>(1, std::min<int64_t>((g->n + 255) / 256, (int64_t)g->sms * 8));
-    backward_walk_kernel<<<wb, 256, 0, s>>>(parent_edge, grad_dist, g->src, grad_w, g->n, g->m, g->ctl);
+    const int64_t work = std::max<int64_t>(g->m, g->n);
+    const int cb = (int)std::max<int64_t>(1, std::min<int64_t>((work + 255) / 256, (int64_t)g->sms * 8));
+    bw_count_kernel<<<cb, 256, 0, s>>>(parent_edge, grad_dist, g->src, g->n, g->m, g->bw_acc, g->bw_cnt,
+                                       g->bw_cnt + g->n, g->bw_cnt + 2 * (size_t)g->n, g->bw_edges, grad_w,
+                                       g->ctl);
+    const int vb = (int)std::max<int64_t>(1, std::min<int64_t>((g->n + 255) / 256, (int64_t)g->sms * 8));
+    bw_walk_kernel<<<vb, 256, 0, s>>>(parent_edge, g->bw_cnt + 2 * (size_t)g->n, g->n, g->bw_acc, g->bw_cnt,
+                                      g->bw_cnt + g->n, grad_w, g->bw_edges, g->ctl);
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e);

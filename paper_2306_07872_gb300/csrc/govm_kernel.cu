@@ -13,10 +13,10 @@
 //              together) and marks beta for every candidate that beats the
 //              distance it read; both are fire-and-forget reductions, so no
 //              warp waits for an atomic's result;
-//      build   beta is consumed in 32-word chunks and compacted into delta
-//              (one entry per marked vertex with an out-edge), one warp
-//              atomicAdd per 128 vertices reserving entries and edge offsets
-//              together;
+//      build   beta is consumed in chunks of up to 32 words and compacted
+//              into delta (one entry per marked vertex with an out-edge), one
+//              warp atomicAdd per 128 vertices reserving entries and edge
+//              offsets together;
 //      each phase ends with a device-wide barrier (bounded wait); the loop
 //      stops when delta is empty (no path changed) or at the step cap;
 //   4. unpack dist / parent / parent_edge.
@@ -91,7 +91,6 @@ struct WarpTile {
 struct BlockShared {
   int32_t tprefix[kMaxInstancesPerLaunch + 1];
   unsigned long long scan[kWarpsPerBlock];
-  unsigned long long base;
   int32_t flag;
   unsigned long long bar_target;  // arrivals that end the next device-wide barrier (thread 0)
   WarpTile wt[kWarpsPerBlock];

@@ -88,3 +88,25 @@ def test_backward_rejects_cyclic_parent_array(dawn):
     gw = torch.empty(3, dtype=torch.float32, device="cuda")
     dawn.dawn_sssp_backward(g.handle, pe, gd, gw)
     assert dawn.dawn_status(g.handle) == dawn.DAWN_ERR_INVALID
+
+
+def test_backward_dense_grad_on_deep_tree(dawn):
+    # every vertex of a grid (tree depth in the hundreds) carries a gradient:
+    # each tree edge is handled once, children before parents
+    wl = gg.grid_f32(160, 0.0, nsrc=1, seed=5)
+    g = dawn.Graph(wl.row_ptr, wl.col, wl.weights)
+    s = int(wl.sources[0])
+    dist, _, pe = g.sssp(s, parent=False, parent_edge=True)
+    cvec = torch.from_numpy(gg.uniform01(11, 0, wl.n).astype(np.float32) + 0.5).cuda()
+    grad_w = torch.empty(wl.m, dtype=torch.float32, device="cuda")
+    for _ in range(2):  # the scratch of the first call is reused by the second
+        dawn.dawn_sssp_backward(g.handle, pe, cvec, grad_w)
+        g.check()
+        pe_np = pe.cpu().numpy()
+        c = cvec.cpu().numpy().astype(np.float64)
+        g_ref = oracle.subtree_grad(wl.row_ptr, wl.col, wl.weights, s, c, parent_edge=pe_np)
+        got = grad_w.cpu().numpy()
+        assert np.all(np.abs(got - g_ref) <= 1e-4 * np.abs(g_ref) + 1e-30)
+        on_tree = np.zeros(wl.m, bool)
+        on_tree[pe_np[pe_np >= 0]] = True
+        assert np.all(got[~on_tree] == 0) and np.all(got[on_tree] > 0)
