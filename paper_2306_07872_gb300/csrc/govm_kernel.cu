@@ -558,10 +558,7 @@ __global__ void __launch_bounds__(kBlockThreads, MINB) govm_kernel(GovmParams p)
   }
 
   // 1. alpha = +inf, beta = {}.
-  for (int32_t i = 0; i < p.k; ++i) {
-    unsigned long long *st = p.state + (size_t)i * p.n;
-    for (long long v = gtid; v < p.n; v += gsize) st[v] = kInfState;
-  }
+  for (long long i = gtid; i < (long long)p.k * p.n; i += gsize) p.state[i] = kInfState;
   for (long long i = gtid; i < (long long)p.k * p.words; i += gsize) p.bitmap[i] = 0u;
   for (long long i = gtid; i < 2LL * p.k; i += gsize) p.tails[i] = 0ull;
   if (!grid_barrier(ctl, p.wait_limit_ns, &sh.flag, &sh.bar_target)) goto finish;
@@ -645,20 +642,37 @@ __global__ void __launch_bounds__(kBlockThreads, MINB) govm_kernel(GovmParams p)
 
   // 4. Outputs (only from a quiescent state: every block left the loop at the
   // same step, after a completed barrier).
+  // State and outputs share the [k][n] layout, so one flat index covers all
+  // instances; each thread handles four elements per round with all their
+  // loads (the parent's tail gather included) in flight together.
   if (quiescent) {
-    for (int32_t i = 0; i < p.k; ++i) {
-      const unsigned long long *st = p.state + (size_t)i * p.n;
-      uint32_t *dist = (uint32_t *)p.dist + (size_t)i * p.n;
-      int32_t *par = p.parent ? p.parent + (size_t)i * p.n : nullptr;
-      int32_t *pe = p.parent_edge ? p.parent_edge + (size_t)i * p.n : nullptr;
-      for (long long v = gtid; v < p.n; v += gsize) {
-        const unsigned long long s = __ldcg(st + v);
-        const uint32_t key = (uint32_t)(s >> 32);
-        const uint32_t e = (uint32_t)s;
-        const bool unreachable = key == Key<WT>::inf;
-        dist[v] = Key<WT>::out(key);
-        if (par) par[v] = unreachable ? -1 : (e == kNoEdge ? (int32_t)v : __ldg(p.src + e));
-        if (pe) pe[v] = (unreachable || e == kNoEdge) ? -1 : (int32_t)e;
+    constexpr int kU = 4;
+    const long long total = (long long)p.k * p.n;
+    uint32_t *dist = (uint32_t *)p.dist;
+    for (long long base = gtid; base < total; base += kU * gsize) {
+      unsigned long long s[kU];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const long long idx = base + u * gsize;
+        s[u] = idx < total ? __ldcg(p.state + idx) : 0ull;
+      }
+      int32_t pv[kU];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const long long idx = base + u * gsize;
+        const uint32_t key = (uint32_t)(s[u] >> 32), e = (uint32_t)s[u];
+        pv[u] = -1;
+        if (p.parent && idx < total && key != Key<WT>::inf)
+          pv[u] = e == kNoEdge ? (int32_t)(idx % p.n) : __ldg(p.src + e);
+      }
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const long long idx = base + u * gsize;
+        if (idx >= total) break;
+        const uint32_t key = (uint32_t)(s[u] >> 32), e = (uint32_t)s[u];
+        dist[idx] = Key<WT>::out(key);
+        if (p.parent) p.parent[idx] = pv[u];
+        if (p.parent_edge) p.parent_edge[idx] = (key == Key<WT>::inf || e == kNoEdge) ? -1 : (int32_t)e;
       }
     }
   }
