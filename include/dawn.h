@@ -212,6 +212,10 @@ int dawn_get_stats(dawn_graph g, dawn_stats *out);
  *                          (0 = as many as the workspace budget allows)
  *   DAWN_OPT_TEST_STALL    1: block 0 waits on a flag nothing sets, so the
  *                          bounded waits run out (tests DAWN_ERR_TIMEOUT)
+ *   DAWN_OPT_TEST_FAIL_ALLOC  N > 0: the N-th next allocation of this
+ *                          handle's workspace (solver, backward scratch,
+ *                          trace) fails with DAWN_ERR_OOM without touching
+ *                          the device (tests the out-of-memory paths); 0 = off
  *   DAWN_OPT_TRACE_STEPS   record up to `value` per-step trace rows in later
  *                          solves (0 = off, the default); allocates
  *   DAWN_OPT_GSVM          1: solve with Algorithm 1 (GSVM, Section 3.2) instead
@@ -229,7 +233,8 @@ enum {
   DAWN_OPT_TRACE_STEPS = 5,
   DAWN_OPT_GSVM = 6,
   DAWN_OPT_CTAS_PER_SM = 7,
-  DAWN_OPT_BATCH = 8
+  DAWN_OPT_BATCH = 8,
+  DAWN_OPT_TEST_FAIL_ALLOC = 9
 };
 int dawn_set_option(dawn_graph g, int option, int64_t value);
 

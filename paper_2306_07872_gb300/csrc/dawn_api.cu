@@ -48,6 +48,7 @@ struct dawn_graph_s {
   int ctas_per_sm = 0;  // kernel build (0 = default)
   int batch = 0;        // instances per msssp launch (0 = automatic)
   int test_stall = 0;
+  int64_t fail_alloc = 0;  // test hook: the fail_alloc-th next workspace allocation fails
   int gsvm = 0;
   int occupancy[2] = {0, 0};  // co-resident CTAs per SM of the 4- and 5-CTA builds (cached)
   int last_k = 0;
@@ -219,6 +220,18 @@ int dalloc(T **p, size_t count) {
   return DAWN_OK;
 }
 
+// Allocation of a handle's workspace (solver, backward, trace), with the
+// DAWN_OPT_TEST_FAIL_ALLOC hook: a host-side stand-in for an out-of-memory
+// device, so the OOM paths are tested without exhausting a shared GPU.
+template <typename T>
+int halloc(dawn_graph g, T **p, size_t count) {
+  if (g->fail_alloc > 0 && --g->fail_alloc == 0) {
+    *p = nullptr;
+    return DAWN_ERR_OOM;
+  }
+  return dalloc(p, count);
+}
+
 void free_workspace(dawn_graph g) {
   cudaFree(g->state);
   cudaFree(g->bitmap);
@@ -253,9 +266,9 @@ int ensure_workspace(dawn_graph g, int32_t k) {
   g->tiles_cap = g->m / dawn::kTile + 2;
   const size_t kn = (size_t)k * g->n;
   int rc;
-  if ((rc = dalloc(&g->state, kn)) || (rc = dalloc(&g->bitmap, (size_t)k * g->words)) ||
-      (rc = dalloc(&g->queue, kn)) || (rc = dalloc(&g->tiles, (size_t)k * g->tiles_cap)) ||
-      (rc = dalloc(&g->tails, (size_t)2 * k))) {
+  if ((rc = halloc(g, &g->state, kn)) || (rc = halloc(g, &g->bitmap, (size_t)k * g->words)) ||
+      (rc = halloc(g, &g->queue, kn)) || (rc = halloc(g, &g->tiles, (size_t)k * g->tiles_cap)) ||
+      (rc = halloc(g, &g->tails, (size_t)2 * k))) {
     free_workspace(g);
     return rc;
   }
@@ -535,8 +548,8 @@ int dawn_sssp_backward(dawn_graph g, const int32_t *parent_edge, const float *gr
   cudaStream_t s = (cudaStream_t)stream;
   if (!g->bw_acc) {
     int rc;
-    if ((rc = dalloc(&g->bw_acc, (size_t)g->n)) || (rc = dalloc(&g->bw_cnt, 3 * (size_t)g->n)) ||
-        (rc = dalloc(&g->bw_edges, 3))) {
+    if ((rc = halloc(g, &g->bw_acc, (size_t)g->n)) || (rc = halloc(g, &g->bw_cnt, 3 * (size_t)g->n)) ||
+        (rc = halloc(g, &g->bw_edges, 3))) {
       cudaFree(g->bw_acc);
       cudaFree(g->bw_cnt);
       g->bw_acc = nullptr;
@@ -608,6 +621,10 @@ int dawn_set_option(dawn_graph g, int option, int64_t value) {
       g->batch = (int)value;
       return DAWN_OK;
     case DAWN_OPT_TEST_STALL: g->test_stall = value != 0; return DAWN_OK;
+    case DAWN_OPT_TEST_FAIL_ALLOC:
+      if (value < 0) return DAWN_ERR_INVALID;
+      g->fail_alloc = value;
+      return DAWN_OK;
     case DAWN_OPT_GSVM: g->gsvm = value != 0; return DAWN_OK;
     case DAWN_OPT_TRACE_STEPS: {
       if (value < 0 || value > (1 << 24)) return DAWN_ERR_INVALID;
@@ -617,7 +634,7 @@ int dawn_set_option(dawn_graph g, int option, int64_t value) {
       g->trace = nullptr;
       g->trace_cap = 0;
       if (value == 0) return DAWN_OK;
-      int rc = dalloc(&g->trace, (size_t)value * 4);
+      int rc = halloc(g, &g->trace, (size_t)value * 4);
       if (rc) return rc;
       if (cudaMemset(g->trace, 0, (size_t)value * 4 * sizeof(unsigned long long)) != cudaSuccess) return DAWN_ERR_CUDA;
       g->trace_cap = (int32_t)value;

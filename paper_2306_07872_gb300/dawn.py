@@ -27,7 +27,7 @@ DAWN_ERR_NOT_CONVERGED, DAWN_ERR_TIMEOUT, DAWN_ERR_BOUNDS = 4, 5, 6
 DAWN_OPT_MAX_STEPS, DAWN_OPT_WAIT_LIMIT_NS, DAWN_OPT_GRID_BLOCKS, DAWN_OPT_TEST_STALL = 1, 2, 3, 4
 DAWN_OPT_TRACE_STEPS = 5
 DAWN_OPT_GSVM = 6
-DAWN_OPT_CTAS_PER_SM, DAWN_OPT_BATCH = 7, 8
+DAWN_OPT_CTAS_PER_SM, DAWN_OPT_BATCH, DAWN_OPT_TEST_FAIL_ALLOC = 7, 8, 9
 DAWN_TUNE_SSSP, DAWN_TUNE_MSSSP, DAWN_TUNE_ROOTS = 0, 1, 2
 DAWN_WEIGHTS_ON_DEVICE, DAWN_WEIGHTS_DEFER_CHECK = 1, 2
 
@@ -321,13 +321,61 @@ class Graph:
     def set_option(self, option: int, value: int):
         dawn_set_option(self.handle, option, value)
 
-    def autotune(self, sources, mode: str = "sssp", reps: int = 3, stream=None) -> dict:
+    def autotune(self, sources, mode: str = "sssp", reps: int = 3, stream=None, cache: str | None = None) -> dict:
         """Pick and keep the fastest launch configuration for `sources`
         (mode "sssp": one dawn_sssp per source; "msssp": one batched solve;
-        "roots": one multi-root solve)."""
+        "roots": one multi-root solve).  With `cache` (a JSON file path) a
+        configuration tuned before for a graph of the same shape class on
+        the same GPU model is applied without timing, and a new one is
+        stored there."""
         m = {"sssp": DAWN_TUNE_SSSP, "msssp": DAWN_TUNE_MSSSP, "roots": DAWN_TUNE_ROOTS}[mode]
+        k = len(sources)
+        key = None
+        if cache is not None:
+            props = torch.cuda.get_device_properties(self.device)
+            key = tune_cache_key(self.n, self.m, self.wtype, mode, k, f"{props.name}/{props.multi_processor_count}")
+            hit = tune_cache_load(cache).get(key)
+            if hit is not None:
+                self.set_option(DAWN_OPT_CTAS_PER_SM, hit["ctas_per_sm"])
+                self.set_option(DAWN_OPT_GRID_BLOCKS, hit["grid_blocks"])
+                self.set_option(DAWN_OPT_BATCH, hit["batch"])
+                return dict(hit, cached=True)
         with torch.cuda.device(self.device):
-            return dawn_autotune(self.handle, m, sources, reps, stream)
+            res = dawn_autotune(self.handle, m, sources, reps, stream)
+        if key is not None:
+            tune_cache_store(cache, key, res)
+        return dict(res, cached=False)
+
+
+def tune_cache_key(n: int, m: int, wtype: int, mode: str, k: int, gpu: str) -> str:
+    """Shape class of a tuning problem: GPU model, weight type, mode and the
+    binary orders of magnitude of n, m, the average degree (half steps) and
+    the source count."""
+    import math
+    lg = lambda x: int(round(math.log2(max(x, 1))))
+    deg = round(2 * math.log2(max(m, 1) / max(n, 1))) / 2 if n > 0 and m > 0 else 0
+    return f"{gpu}|w{wtype}|{mode}|n2^{lg(n)}|m2^{lg(m)}|d2^{deg}|k2^{lg(k)}"
+
+
+def tune_cache_load(path: str) -> dict:
+    import json
+    try:
+        with open(path) as f:
+            data = json.load(f)
+        return data if isinstance(data, dict) else {}
+    except (OSError, ValueError):
+        return {}
+
+
+def tune_cache_store(path: str, key: str, result: dict):
+    """Adds one entry; the file is replaced atomically."""
+    import json
+    data = tune_cache_load(path)
+    data[key] = {f: result[f] for f in ("ctas_per_sm", "grid_blocks", "batch", "best_ms", "default_ms")}
+    tmp = f"{path}.tmp{os.getpid()}"
+    with open(tmp, "w") as f:
+        json.dump(data, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
 
 
 class DawnSSSP(torch.autograd.Function):

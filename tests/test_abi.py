@@ -73,3 +73,22 @@ def test_oracle_is_not_imported_by_the_package():
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
                 assert "graphgen" not in text, f
+
+
+def test_tune_cache_keys_and_store(tmp_path):
+    from paper_2306_07872_gb300 import dawn as d
+    k1 = d.tune_cache_key(4194304, 65243778, 0, "sssp", 8, "GB300/152")
+    assert k1 == d.tune_cache_key(4000000, 66000000, 0, "sssp", 8, "GB300/152")  # same shape class
+    assert k1 != d.tune_cache_key(4194304, 65243778, 1, "sssp", 8, "GB300/152")  # weight type
+    assert k1 != d.tune_cache_key(4194304, 16769024, 0, "sssp", 8, "GB300/152")  # degree
+    assert k1 != d.tune_cache_key(4194304, 65243778, 0, "msssp", 8, "GB300/152")  # mode
+    assert k1 != d.tune_cache_key(4194304, 65243778, 0, "sssp", 8, "B200/148")  # GPU model
+    path = str(tmp_path / "tune.json")
+    assert d.tune_cache_load(path) == {}
+    res = {"ctas_per_sm": 4, "grid_blocks": 608, "batch": 0, "best_ms": 1.0, "default_ms": 1.1, "candidates": 11}
+    d.tune_cache_store(path, k1, res)
+    d.tune_cache_store(path, "other", dict(res, grid_blocks=0))
+    got = d.tune_cache_load(path)
+    assert got[k1]["grid_blocks"] == 608 and got["other"]["grid_blocks"] == 0 and "candidates" not in got[k1]
+    (tmp_path / "bad.json").write_text("not json")
+    assert d.tune_cache_load(str(tmp_path / "bad.json")) == {}

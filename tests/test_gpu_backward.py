@@ -110,3 +110,21 @@ def test_backward_dense_grad_on_deep_tree(dawn):
         on_tree = np.zeros(wl.m, bool)
         on_tree[pe_np[pe_np >= 0]] = True
         assert np.all(got[~on_tree] == 0) and np.all(got[on_tree] > 0)
+
+
+def test_backward_scratch_allocation_failure(dawn):
+    wl = gg.rmat_f32_diff(scale=10, edge_factor=4, ntargets=4, seed=6)
+    g = dawn.Graph(wl.row_ptr, wl.col, wl.weights)
+    dist, _, pe = g.sssp(0, parent=False, parent_edge=True)
+    gd = torch.ones(wl.n, dtype=torch.float32, device="cuda")
+    gw = torch.empty(wl.m, dtype=torch.float32, device="cuda")
+    g.set_option(dawn.DAWN_OPT_TEST_FAIL_ALLOC, 2)  # the second scratch array
+    with pytest.raises(dawn.DawnError) as e:
+        dawn.dawn_sssp_backward(g.handle, pe, gd, gw)
+    assert e.value.code == dawn.DAWN_ERR_OOM
+    dawn.dawn_sssp_backward(g.handle, pe, gd, gw)  # allocates again and runs
+    g.check()
+    pe_np = pe.cpu().numpy()
+    c = np.where(np.isfinite(dist.cpu().numpy()), 1.0, 0.0)
+    g_ref = oracle.subtree_grad(wl.row_ptr, wl.col, wl.weights, 0, c, parent_edge=pe_np)
+    assert np.all(np.abs(gw.cpu().numpy() - g_ref) <= 1e-4 * np.abs(g_ref) + 1e-30)

@@ -283,3 +283,28 @@ def test_host_and_device_inputs_agree(dawn):
     s = int(wl.sources[0])
     for a, b in zip(solve(g1, s), solve(g2, s)):
         assert np.array_equal(a, b)
+
+
+def test_allocation_failure_reports_oom_and_handle_recovers(dawn):
+    # host-side injection (no device is driven out of memory): the N-th next
+    # workspace allocation fails; the call reports DAWN_ERR_OOM, frees what it
+    # had, and the handle stays usable
+    wl = gg.rmat_u32(11, 8, nsrc=1, seed=12)
+    s = int(wl.sources[0])
+    for nth in (1, 3, 5):
+        g = dawn.Graph(wl.row_ptr, wl.col, wl.weights)
+        g.set_option(dawn.DAWN_OPT_TEST_FAIL_ALLOC, nth)
+        with pytest.raises(dawn.DawnError) as e:
+            g.sssp(s)
+        assert e.value.code == dawn.DAWN_ERR_OOM
+        d, p, pe = solve(g, s)
+        assert_exact(wl.row_ptr, wl.col, wl.weights, s, d, p, pe)
+    g = dawn.Graph(wl.row_ptr, wl.col, wl.weights)
+    g.set_option(dawn.DAWN_OPT_TEST_FAIL_ALLOC, 1)
+    with pytest.raises(dawn.DawnError) as e:
+        dawn.dawn_reserve(g.handle, 8)
+    assert e.value.code == dawn.DAWN_ERR_OOM
+    dist, _ = g.msssp(wl.sources)
+    assert np.array_equal(dist[0].cpu().numpy(), oracle.dijkstra(wl.row_ptr, wl.col, wl.weights, s))
+    with pytest.raises(dawn.DawnError):
+        g.set_option(dawn.DAWN_OPT_TEST_FAIL_ALLOC, -1)

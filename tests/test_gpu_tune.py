@@ -141,3 +141,18 @@ def test_batched_counters_cover_every_launch(dawn):
     for key in ("edges_scanned", "updates", "frontier_sum"):
         ratio = per[5][key] / per[0][key]
         assert 0.8 < ratio < 1.25, (key, per)
+
+
+def test_autotune_cache_reuses_a_stored_configuration(dawn, tmp_path):
+    wl = gg.rmat_u32(12, 16, nsrc=4, seed=30)
+    path = str(tmp_path / "tune.json")
+    g = dawn.Graph(wl.row_ptr, wl.col, wl.weights)
+    first = g.autotune(wl.sources, mode="sssp", reps=1, cache=path)
+    assert first["cached"] is False
+    h = dawn.Graph(wl.row_ptr, wl.col, wl.weights)
+    again = h.autotune(wl.sources, mode="sssp", reps=1, cache=path)
+    assert again["cached"] is True
+    for f in ("ctas_per_sm", "grid_blocks", "batch"):
+        assert again[f] == first[f]
+    for s in wl.sources:
+        exact(h, wl.row_ptr, wl.col, wl.weights, s)
