@@ -212,6 +212,16 @@ int dawn_get_stats(dawn_graph g, dawn_stats *out);
  *                          (0 = as many as the workspace budget allows)
  *   DAWN_OPT_TEST_STALL    1: block 0 waits on a flag nothing sets, so the
  *                          bounded waits run out (tests DAWN_ERR_TIMEOUT)
+ *   DAWN_OPT_SMALL_PATH    DAWN_SMALL_AUTO (default): a graph whose solver
+ *                          state and CSR fit in one block's shared memory
+ *                          (about 12 bytes per vertex + 8 per edge within
+ *                          the device's opt-in limit, 227 KB on GB300) is
+ *                          solved by a kernel with one block per instance
+ *                          and everything on-chip, so no step needs a
+ *                          device-wide barrier; DAWN_SMALL_NEVER: always the
+ *                          persistent kernel; DAWN_SMALL_WHEN_STATE_FITS:
+ *                          the small kernel whenever the state fits (the CSR
+ *                          is then read from global memory).  Same results.
  *   DAWN_OPT_TEST_FAIL_ALLOC  N > 0: the N-th next allocation of this
  *                          handle's workspace (solver, backward scratch,
  *                          trace) fails with DAWN_ERR_OOM without touching
@@ -234,8 +244,10 @@ enum {
   DAWN_OPT_GSVM = 6,
   DAWN_OPT_CTAS_PER_SM = 7,
   DAWN_OPT_BATCH = 8,
-  DAWN_OPT_TEST_FAIL_ALLOC = 9
+  DAWN_OPT_TEST_FAIL_ALLOC = 9,
+  DAWN_OPT_SMALL_PATH = 10
 };
+enum { DAWN_SMALL_AUTO = 0, DAWN_SMALL_NEVER = 1, DAWN_SMALL_WHEN_STATE_FITS = 2 };
 int dawn_set_option(dawn_graph g, int option, int64_t value);
 
 /*
@@ -245,10 +257,12 @@ int dawn_set_option(dawn_graph g, int option, int64_t value);
  * Times the workload under candidate launch configurations and stores the
  * fastest as the handle's options (DAWN_OPT_CTAS_PER_SM, DAWN_OPT_GRID_BLOCKS
  * and, in DAWN_TUNE_MSSSP mode, DAWN_OPT_BATCH), which then apply to every
- * later solve on the handle.  The candidates are the two kernel builds
- * (4 or 5 CTAs per SM) times the grid sizes {all co-resident CTAs, 3/4, 1/2,
- * 1/4 of them, one per SM, the automatic size}, times, in DAWN_TUNE_MSSSP
- * mode, the batch sizes {largest, 1/2, 1/4 of it}.  Results do not depend on
+ * later solve on the handle.  The candidates are the default options, the
+ * two builds of the persistent kernel (4 or 5 CTAs per SM) times the grid
+ * sizes {all co-resident CTAs, 3/4, 1/2, 1/4 of them, one per SM, the
+ * automatic size}, times, in DAWN_TUNE_MSSSP mode, the batch sizes {largest,
+ * 1/2, 1/4 of it}, and the small-graph kernel when the graph's solver state
+ * fits in shared memory (DAWN_OPT_SMALL_PATH).  Results do not depend on
  * the configuration (the solver's fixpoint is order-independent); only the
  * time does.
  *   mode     DAWN_TUNE_SSSP: dawn_sssp from each source in turn;
@@ -271,6 +285,7 @@ typedef struct {
   int32_t candidates;   /* configurations timed */
   float best_ms;        /* median workload time with the chosen configuration */
   float default_ms;     /* median workload time with the default options */
+  int32_t small_path;   /* chosen DAWN_OPT_SMALL_PATH */
 } dawn_tuning;
 
 enum { DAWN_TUNE_SSSP = 0, DAWN_TUNE_MSSSP = 1, DAWN_TUNE_ROOTS = 2 };

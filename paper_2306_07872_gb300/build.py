@@ -10,7 +10,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libdawn.so")
-SOURCES = ["govm_kernel.cu", "dawn_api.cu", "dawn_tune.cu"]
+SOURCES = ["govm_kernel.cu", "govm_small.cu", "dawn_api.cu", "dawn_tune.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE]
 

@@ -47,6 +47,7 @@ struct dawn_graph_s {
   int grid_blocks = 0;
   int ctas_per_sm = 0;  // kernel build (0 = default)
   int batch = 0;        // instances per msssp launch (0 = automatic)
+  int small_path = 0;   // DAWN_OPT_SMALL_PATH
   int test_stall = 0;
   int64_t fail_alloc = 0;  // test hook: the fail_alloc-th next workspace allocation fails
   int gsvm = 0;
@@ -307,9 +308,20 @@ uint32_t weight_limit(int wtype) {
 // One persistent launch.  `accumulate` (later launches of one batched call)
 // keeps the status and the counters of the earlier launches: only the
 // barrier word and the per-step change flags start again from zero.
+// The small-graph kernel's mode for this handle and call: 0 = not used,
+// 1 = with the solver state in shared memory, 2 = with the CSR there too.
+int small_mode(dawn_graph g) {
+  if (g->small_path == DAWN_SMALL_NEVER || g->gsvm || g->test_stall || g->trace) return 0;
+  const size_t limit = dawn::small_smem_limit();
+  if (dawn::small_layout(g->n, g->m, true).total <= limit) return 2;
+  if (g->small_path == DAWN_SMALL_WHEN_STATE_FITS && dawn::small_layout(g->n, g->m, false).total <= limit) return 1;
+  return 0;
+}
+
 int run_solve(dawn_graph g, const int32_t *seeds, int32_t nseeds, int32_t source, int32_t k, int roots_mode,
               void *dist, int32_t *parent, int32_t *parent_edge, cudaStream_t stream, bool accumulate = false) {
-  int rc = ensure_workspace(g, k);
+  const int small = small_mode(g);
+  int rc = small ? DAWN_OK : ensure_workspace(g, k);  // the small kernel keeps its state on-chip
   if (rc) return rc;
   GovmParams p = {};
   p.row_ptr = g->row_ptr;
@@ -351,7 +363,8 @@ int run_solve(dawn_graph g, const int32_t *seeds, int32_t nseeds, int32_t source
   if (e == cudaSuccess && g->trace)
     e = cudaMemsetAsync(g->trace, 0, (size_t)g->trace_cap * 4 * sizeof(unsigned long long), stream);
   if (e != cudaSuccess) return cuda_fail(e);
-  e = dawn::launch_govm(p, g->wtype, kernel_ctas(g), grid_for(g, k), stream);
+  e = small ? dawn::launch_govm_small(p, g->wtype, roots_mode ? 1 : k, small == 2, stream)
+            : dawn::launch_govm(p, g->wtype, kernel_ctas(g), grid_for(g, k), stream);
   if (e != cudaSuccess) return cuda_fail(e);
   g->last_stream = stream;
   return DAWN_OK;
@@ -420,6 +433,8 @@ int launch_limits(dawn_graph g, LaunchLimits *out) {
   out->ctas_per_sm = g->ctas_per_sm;
   out->grid_blocks = g->grid_blocks;
   out->batch = g->batch;
+  out->small_path = g->small_path;
+  out->small_state_fits = dawn::small_layout(g->n, g->m, false).total <= dawn::small_smem_limit();
   return DAWN_OK;
 }
 }  // namespace dawn
@@ -619,6 +634,10 @@ int dawn_set_option(dawn_graph g, int option, int64_t value) {
     case DAWN_OPT_BATCH:
       if (value < 0 || value > 0x7FFFFFFF) return DAWN_ERR_INVALID;
       g->batch = (int)value;
+      return DAWN_OK;
+    case DAWN_OPT_SMALL_PATH:
+      if (value < 0 || value > DAWN_SMALL_WHEN_STATE_FITS) return DAWN_ERR_INVALID;
+      g->small_path = (int)value;
       return DAWN_OK;
     case DAWN_OPT_TEST_STALL: g->test_stall = value != 0; return DAWN_OK;
     case DAWN_OPT_TEST_FAIL_ALLOC:

@@ -98,6 +98,17 @@ struct GovmParams {
 cudaError_t launch_govm(const GovmParams &p, int wtype, int ctas_per_sm, int grid_blocks, cudaStream_t stream);
 int govm_max_blocks_per_sm(int wtype, int ctas_per_sm);
 
+// Small-graph kernel (govm_small.cu): one block per instance with the whole
+// solver state in shared memory (and the CSR when it fits).
+constexpr int kSmallThreads = 1024;
+constexpr int kSmallWarps = kSmallThreads / 32;
+struct SmallLayout {  // byte offsets in the block's dynamic shared memory
+  size_t state, bitmap, front, scan, row_ptr, cw, total;
+};
+__host__ __device__ SmallLayout small_layout(int32_t n, int64_t m, bool csr);
+size_t small_smem_limit();  // the device's opt-in shared memory per block
+cudaError_t launch_govm_small(const GovmParams &p, int wtype, int32_t blocks, bool csr_in_smem, cudaStream_t stream);
+
 // Launch limits and current launch options of a handle (dawn_api.cu), for
 // the autotuner (dawn_tune.cu), which otherwise uses only the public API.
 struct LaunchLimits {
@@ -108,6 +119,8 @@ struct LaunchLimits {
   int ctas_per_sm;      // current DAWN_OPT_CTAS_PER_SM
   int grid_blocks;      // current DAWN_OPT_GRID_BLOCKS
   int batch;            // current DAWN_OPT_BATCH
+  int small_path;       // current DAWN_OPT_SMALL_PATH
+  int small_state_fits;  // the small-graph kernel could hold this graph's solver state
 };
 int launch_limits(dawn_graph g, LaunchLimits *out);
 

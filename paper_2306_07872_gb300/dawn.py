@@ -27,7 +27,8 @@ DAWN_ERR_NOT_CONVERGED, DAWN_ERR_TIMEOUT, DAWN_ERR_BOUNDS = 4, 5, 6
 DAWN_OPT_MAX_STEPS, DAWN_OPT_WAIT_LIMIT_NS, DAWN_OPT_GRID_BLOCKS, DAWN_OPT_TEST_STALL = 1, 2, 3, 4
 DAWN_OPT_TRACE_STEPS = 5
 DAWN_OPT_GSVM = 6
-DAWN_OPT_CTAS_PER_SM, DAWN_OPT_BATCH, DAWN_OPT_TEST_FAIL_ALLOC = 7, 8, 9
+DAWN_OPT_CTAS_PER_SM, DAWN_OPT_BATCH, DAWN_OPT_TEST_FAIL_ALLOC, DAWN_OPT_SMALL_PATH = 7, 8, 9, 10
+DAWN_SMALL_AUTO, DAWN_SMALL_NEVER, DAWN_SMALL_WHEN_STATE_FITS = 0, 1, 2
 DAWN_TUNE_SSSP, DAWN_TUNE_MSSSP, DAWN_TUNE_ROOTS = 0, 1, 2
 DAWN_WEIGHTS_ON_DEVICE, DAWN_WEIGHTS_DEFER_CHECK = 1, 2
 
@@ -48,7 +49,8 @@ class _Stats(ctypes.Structure):
 
 class _Tuning(ctypes.Structure):
     _fields_ = [("ctas_per_sm", ctypes.c_int32), ("grid_blocks", ctypes.c_int32), ("batch", ctypes.c_int32),
-                ("candidates", ctypes.c_int32), ("best_ms", ctypes.c_float), ("default_ms", ctypes.c_float)]
+                ("candidates", ctypes.c_int32), ("best_ms", ctypes.c_float), ("default_ms", ctypes.c_float),
+                ("small_path", ctypes.c_int32)]
 
 
 _lib = None
@@ -339,6 +341,7 @@ class Graph:
                 self.set_option(DAWN_OPT_CTAS_PER_SM, hit["ctas_per_sm"])
                 self.set_option(DAWN_OPT_GRID_BLOCKS, hit["grid_blocks"])
                 self.set_option(DAWN_OPT_BATCH, hit["batch"])
+                self.set_option(DAWN_OPT_SMALL_PATH, hit.get("small_path", DAWN_SMALL_AUTO))
                 return dict(hit, cached=True)
         with torch.cuda.device(self.device):
             res = dawn_autotune(self.handle, m, sources, reps, stream)
@@ -371,7 +374,8 @@ def tune_cache_store(path: str, key: str, result: dict):
     """Adds one entry; the file is replaced atomically."""
     import json
     data = tune_cache_load(path)
-    data[key] = {f: result[f] for f in ("ctas_per_sm", "grid_blocks", "batch", "best_ms", "default_ms")}
+    data[key] = {f: result[f] for f in ("ctas_per_sm", "grid_blocks", "batch", "small_path", "best_ms", "default_ms")
+                 if f in result}
     tmp = f"{path}.tmp{os.getpid()}"
     with open(tmp, "w") as f:
         json.dump(data, f, indent=1, sort_keys=True)

@@ -18,6 +18,18 @@ def dawn():
     return pkg
 
 
+# every test runs on both kernels: the small-graph one (where the graph fits
+# on-chip) and the persistent one
+@pytest.fixture(params=["auto", "persistent"])
+def Graph(dawn, request):
+    def make(*args):
+        g = dawn.Graph(*args)
+        if request.param == "persistent":
+            g.set_option(dawn.DAWN_OPT_SMALL_PATH, dawn.DAWN_SMALL_NEVER)
+        return g
+    return make
+
+
 def exact_rows(wl, sources, dist, parent):
     for i, s in enumerate(sources):
         d_ref, p_ref, _ = oracle.sssp(wl.row_ptr, wl.col, wl.weights, int(s))
@@ -26,9 +38,9 @@ def exact_rows(wl, sources, dist, parent):
             assert np.array_equal(parent[i], p_ref), i
 
 
-def test_msssp_matches_single_solves(dawn):
+def test_msssp_matches_single_solves(dawn, Graph):
     wl = gg.rmat_u32(12, 16, nsrc=64, seed=3)
-    g = dawn.Graph(wl.row_ptr, wl.col, wl.weights)
+    g = Graph(wl.row_ptr, wl.col, wl.weights)
     dist, par = g.msssp(wl.sources)
     dist, par = dist.cpu().numpy(), par.cpu().numpy()
     exact_rows(wl, wl.sources, dist, par)
@@ -37,38 +49,38 @@ def test_msssp_matches_single_solves(dawn):
         assert np.array_equal(d1.cpu().numpy(), dist[i]) and np.array_equal(p1.cpu().numpy(), par[i])
 
 
-def test_msssp_f32_and_duplicate_sources(dawn):
+def test_msssp_f32_and_duplicate_sources(dawn, Graph):
     wl = gg.grid_f32(48, 0.01, nsrc=5, seed=2)
     src = np.concatenate([wl.sources, wl.sources[:2]])
-    g = dawn.Graph(wl.row_ptr, wl.col, wl.weights)
+    g = Graph(wl.row_ptr, wl.col, wl.weights)
     dist, par = g.msssp(src)
     exact_rows(wl, src, dist.cpu().numpy(), par.cpu().numpy())
 
 
-def test_msssp_chunks_beyond_one_launch(dawn):
+def test_msssp_chunks_beyond_one_launch(dawn, Graph):
     # k larger than the per-launch instance limit: several persistent launches
     wl = gg.tiny_er(n=300, avg_deg=6, seed=5)
     src = np.arange(1500, dtype=np.int32) % 300
-    g = dawn.Graph(wl.row_ptr, wl.col, wl.weights)
+    g = Graph(wl.row_ptr, wl.col, wl.weights)
     dist, _ = g.msssp(src, parent=False)
     D = oracle.floyd_warshall(wl.row_ptr, wl.col, wl.weights)
     assert np.array_equal(dist.cpu().numpy(), D[src])
 
 
-def test_apsp_small(dawn):
+def test_apsp_small(dawn, Graph):
     # APSP = msssp over every vertex (Section 3.4); compare with Floyd-Warshall
     rp, cl, w = gg.random_small(200, 1600, 7, kind="dyadic", wlo=0, whi=6)
-    g = dawn.Graph(rp, cl, w)
+    g = Graph(rp, cl, w)
     dist, _ = g.msssp(np.arange(200, dtype=np.int32), parent=False)
     D = oracle.floyd_warshall(rp, cl, w)
     assert np.array_equal(dist.cpu().numpy().view(np.uint32), D.view(np.uint32))
 
 
-def test_apsp_medium_sampled_rows(dawn):
+def test_apsp_medium_sampled_rows(dawn, Graph):
     # all 4096 sources of an ER graph in chunked batched launches; sampled
     # rows bit-exact to Dijkstra, every sampled row certified
     wl = gg.tiny_er(n=4096, avg_deg=8, seed=11)
-    g = dawn.Graph(wl.row_ptr, wl.col, wl.weights)
+    g = Graph(wl.row_ptr, wl.col, wl.weights)
     dist, par = g.msssp(np.arange(wl.n, dtype=np.int32))
     dist = dist.cpu().numpy()
     par = par.cpu().numpy()
@@ -79,9 +91,9 @@ def test_apsp_medium_sampled_rows(dawn):
         assert np.array_equal(par[s], oracle.parent_vertices(wl.row_ptr, s, d_ref, pe, "u32")), s
 
 
-def test_roots_on_uneven_batch(dawn):
+def test_roots_on_uneven_batch(dawn, Graph):
     wl = gg.er_batch(count=12, nlo=100, nhi=20000, dlo=4, dhi=32, seed=6)
-    g = dawn.Graph(wl.row_ptr, wl.col, wl.weights)
+    g = Graph(wl.row_ptr, wl.col, wl.weights)
     d, p, pe = g.sssp_roots(wl.sources, parent=True, parent_edge=True)
     d_ref = oracle.dijkstra(wl.row_ptr, wl.col, wl.weights, wl.sources)
     pe_ref = oracle.parent_edges(wl.row_ptr, wl.col, wl.weights, wl.sources, d_ref)
@@ -96,10 +108,10 @@ def test_roots_on_uneven_batch(dawn):
         assert np.array_equal(d1.cpu().numpy()[sl], d_ref[sl])
 
 
-def test_roots_duplicates_and_invalid(dawn):
+def test_roots_duplicates_and_invalid(dawn, Graph):
     wl = gg.rmat_u32(10, 8, nsrc=4, seed=1)
     roots = np.array([wl.sources[0], wl.sources[1], wl.sources[0]], np.int32)
-    g = dawn.Graph(wl.row_ptr, wl.col, wl.weights)
+    g = Graph(wl.row_ptr, wl.col, wl.weights)
     d, p, _ = g.sssp_roots(roots)
     d_ref = oracle.dijkstra(wl.row_ptr, wl.col, wl.weights, roots)
     assert np.array_equal(d.cpu().numpy(), d_ref)
@@ -107,9 +119,9 @@ def test_roots_duplicates_and_invalid(dawn):
         g.sssp_roots(np.array([0, wl.n], np.int32))
 
 
-def test_msssp_captured_in_cuda_graph(dawn):
+def test_msssp_captured_in_cuda_graph(dawn, Graph):
     wl = gg.rmat_u32(11, 8, nsrc=16, seed=8)
-    g = dawn.Graph(wl.row_ptr, wl.col, wl.weights)
+    g = Graph(wl.row_ptr, wl.col, wl.weights)
     dawn.dawn_reserve(g.handle, 16)
     src = torch.from_numpy(wl.sources).cuda()
     dist = torch.empty((16, wl.n), dtype=torch.uint32, device="cuda")

@@ -25,6 +25,18 @@ def dawn():
     return pkg
 
 
+# parity tests run on both kernels: the small-graph one (graphs that fit
+# on-chip; others fall back to the persistent kernel) and the persistent one
+@pytest.fixture(params=["auto", "persistent"])
+def Graph(dawn, request):
+    def make(*args):
+        g = dawn.Graph(*args)
+        if request.param == "persistent":
+            g.set_option(dawn.DAWN_OPT_SMALL_PATH, dawn.DAWN_SMALL_NEVER)
+        return g
+    return make
+
+
 def bits(a):
     a = np.asarray(a)
     return a.view(np.uint32) if a.dtype in (np.float32, np.uint32, np.int32) else a
@@ -45,18 +57,18 @@ def assert_exact(rp, cl, w, s, d, p, pe):
 
 # ------------------------------------------------------------ tiny workload
 
-def test_tiny_er_source0_exact_and_fw(dawn):
+def test_tiny_er_source0_exact_and_fw(dawn, Graph):
     wl = gg.tiny_er()
-    g = dawn.Graph(wl.row_ptr, wl.col, wl.weights)
+    g = Graph(wl.row_ptr, wl.col, wl.weights)
     d, p, pe = solve(g, 0)
     assert_exact(wl.row_ptr, wl.col, wl.weights, 0, d, p, pe)
     D = oracle.floyd_warshall(wl.row_ptr, wl.col, wl.weights)
     assert np.array_equal(d, D[0])
 
 
-def test_tiny_er_many_sources(dawn):
+def test_tiny_er_many_sources(dawn, Graph):
     wl = gg.tiny_er()
-    g = dawn.Graph(wl.row_ptr, wl.col, wl.weights)
+    g = Graph(wl.row_ptr, wl.col, wl.weights)
     D = oracle.floyd_warshall(wl.row_ptr, wl.col, wl.weights)
     for s in range(0, 1024, 37):
         d, p, pe = solve(g, s)
@@ -67,37 +79,37 @@ def test_tiny_er_many_sources(dawn):
 # ------------------------------------------------- several tiles, ragged tails
 
 @pytest.mark.parametrize("scale,ef,seed", [(10, 4, 1), (12, 8, 2), (14, 16, 3)])
-def test_rmat_u32_exact(dawn, scale, ef, seed):
+def test_rmat_u32_exact(dawn, Graph, scale, ef, seed):
     wl = gg.rmat_u32(scale, ef, nsrc=4, seed=seed)
-    g = dawn.Graph(wl.row_ptr, wl.col, wl.weights)
+    g = Graph(wl.row_ptr, wl.col, wl.weights)
     for s in wl.sources:
         d, p, pe = solve(g, int(s))
         assert_exact(wl.row_ptr, wl.col, wl.weights, int(s), d, p, pe)
 
 
 @pytest.mark.parametrize("side,seed", [(32, 0), (100, 1), (257, 2)])
-def test_grid_f32_exact(dawn, side, seed):
+def test_grid_f32_exact(dawn, Graph, side, seed):
     wl = gg.grid_f32(side, 0.01, nsrc=3, seed=seed)
-    g = dawn.Graph(wl.row_ptr, wl.col, wl.weights)
+    g = Graph(wl.row_ptr, wl.col, wl.weights)
     for s in wl.sources:
         d, p, pe = solve(g, int(s))
         assert_exact(wl.row_ptr, wl.col, wl.weights, int(s), d, p, pe)
 
 
-def test_rmat_f32_exact(dawn):
+def test_rmat_f32_exact(dawn, Graph):
     wl = gg.rmat_f32_diff(scale=13, edge_factor=16, ntargets=8, seed=2)
-    g = dawn.Graph(wl.row_ptr, wl.col, wl.weights)
+    g = Graph(wl.row_ptr, wl.col, wl.weights)
     d, p, pe = solve(g, 0)
     assert_exact(wl.row_ptr, wl.col, wl.weights, 0, d, p, pe)
 
 
-def test_rmat_f32_weights_down_to_zero_exact(dawn):
+def test_rmat_f32_weights_down_to_zero_exact(dawn, Graph):
     # the paper's comparative weights (Section 4.2): fp32 uniform in [0, 2];
     # tiny weights make fl(d + w) == d ties, which the parent rule resolves
     rp, cl = gg.rmat(12, 16, seed=4)
     w = gg.weights_f32_uniform(len(cl), 0.0, 2.0, seed=8)
     w[::97] = np.float32(0.0)
-    g = dawn.Graph(rp, cl, w)
+    g = Graph(rp, cl, w)
     src, _, _ = gg.wcc_sources(rp, cl, 3, seed=2)
     for s in src:
         d, p, pe = solve(g, int(s))
@@ -125,10 +137,10 @@ def test_gsvm_option_same_result_more_work(dawn, kind):
         assert st_gsvm["steps"] >= 2 and ost["converged"] == 1
 
 
-def test_unit_weights_bfs_and_mu_one(dawn):
+def test_unit_weights_bfs_and_mu_one(dawn, Graph):
     # Section 4.2: unit weights find every path once (mu = 1)
     wl = gg.rmat_u32(13, 8, nsrc=2, seed=7, wlo=1, whi=1)
-    g = dawn.Graph(wl.row_ptr, wl.col, wl.weights)
+    g = Graph(wl.row_ptr, wl.col, wl.weights)
     for s in wl.sources:
         d, p, pe = solve(g, int(s))
         assert_exact(wl.row_ptr, wl.col, wl.weights, int(s), d, p, pe)
@@ -137,7 +149,7 @@ def test_unit_weights_bfs_and_mu_one(dawn):
         assert st["updates"] == reached - 1
 
 
-def test_hub_rows_span_many_tiles(dawn):
+def test_hub_rows_span_many_tiles(dawn, Graph):
     # a star with 5000 leaves (20 tiles in one row) feeding a path, plus
     # leaves with parallel edges and self-loops
     n = 6000
@@ -151,58 +163,58 @@ def test_hub_rows_span_many_tiles(dawn):
         edges.append((v, v)); ws.append(0)
         edges.append((v, 5000)); ws.append(2)
     rp, cl, w = gg.csr_from_edges(n, edges, ws)
-    g = dawn.Graph(rp, cl, w)
+    g = Graph(rp, cl, w)
     d, p, pe = solve(g, 0)
     assert_exact(rp, cl, w, 0, d, p, pe)
 
 
-def test_many_degree_one_frontier(dawn):
+def test_many_degree_one_frontier(dawn, Graph):
     # binary tree (frontier of many out-degree-1/2 vertices: up to 257 entries per tile)
     n = 1 << 15
     edges = [(v, c) for v in range(n) for c in (2 * v + 1, 2 * v + 2) if c < n]
     ws = [(a * 31 + b * 17) % 50 + 1 for a, b in edges]
     rp, cl, w = gg.csr_from_edges(n, edges, ws)
-    g = dawn.Graph(rp, cl, w)
+    g = Graph(rp, cl, w)
     d, p, pe = solve(g, 0)
     assert_exact(rp, cl, w, 0, d, p, pe)
 
 
 # ----------------------------------------------------------------- edge cases
 
-def test_edge_cases(dawn):
+def test_edge_cases(dawn, Graph):
     # n = 1, m = 0
-    g = dawn.Graph(np.array([0, 0], np.int32), np.zeros(0, np.int32), np.zeros(0, np.uint32))
+    g = Graph(np.array([0, 0], np.int32), np.zeros(0, np.int32), np.zeros(0, np.uint32))
     d, p, pe = solve(g, 0)
     assert d.tolist() == [0] and p.tolist() == [0] and pe.tolist() == [-1]
     # source with out-degree 0, unreachable parts, zero weight into the source
     rp, cl, w = gg.csr_from_edges(5, [(0, 1), (1, 0), (1, 2), (4, 3)], [0, 0, 5, 1])
-    g = dawn.Graph(rp, cl, w)
+    g = Graph(rp, cl, w)
     for s in range(5):
         assert_exact(rp, cl, w, s, *solve(g, s))
     # fp32 left-fold rounding: 2^24 + 1 + 1 beats 2^24 + 2
     t24 = np.float32(2.0 ** 24)
     rp, cl, w = gg.csr_from_edges(4, [(0, 1), (1, 2), (2, 3), (0, 3)], [t24, 1, 1, t24 + np.float32(2)], np.float32)
-    g = dawn.Graph(rp, cl, w)
+    g = Graph(rp, cl, w)
     d, p, pe = solve(g, 0)
     assert d[3] == t24 and p[3] == 2
     assert_exact(rp, cl, w, 0, d, p, pe)
     # large uint32 weights: n * max(w) just below the sentinel
     big = (0xFFFFFFFE // 4)
     rp, cl, w = gg.csr_from_edges(4, [(0, 1), (1, 2), (2, 3)], [big, big, big])
-    g = dawn.Graph(rp, cl, w)
+    g = Graph(rp, cl, w)
     assert_exact(rp, cl, w, 0, *solve(g, 0))
     # zero-weight ties (the parent rule may form a cycle; both sides agree)
     rp, cl, w = gg.csr_from_edges(6, [(1, 2), (2, 1), (5, 1), (5, 2)], [0, 0, 1, 1])
-    g = dawn.Graph(rp, cl, w)
+    g = Graph(rp, cl, w)
     assert_exact(rp, cl, w, 5, *solve(g, 5))
 
 
 @pytest.mark.parametrize("seed", range(12))
-def test_random_small_multigraphs(dawn, seed):
+def test_random_small_multigraphs(dawn, Graph, seed):
     kind = ["u32", "f32", "dyadic"][seed % 3]
     rp, cl, w = gg.random_small(60 + seed * 13, 400 + seed * 50, seed, kind=kind, wlo=0 if kind != "f32" else 0.0,
                                 whi=9, self_loops=True)
-    g = dawn.Graph(rp, cl, w)
+    g = Graph(rp, cl, w)
     for s in (0, 3, 17):
         assert_exact(rp, cl, w, s, *solve(g, s))
 
@@ -235,9 +247,9 @@ def test_invalid_inputs_rejected(dawn):
     assert d.cpu().tolist() == [1, 0]
 
 
-def test_step_cap_reports_not_converged(dawn):
+def test_step_cap_reports_not_converged(dawn, Graph):
     rp, cl, w = gg.csr_from_edges(5, [(i, i + 1) for i in range(4)], [1, 1, 1, 1])
-    g = dawn.Graph(rp, cl, w)
+    g = Graph(rp, cl, w)
     g.set_option(dawn.DAWN_OPT_MAX_STEPS, 2)
     with pytest.raises(dawn.DawnError) as e:
         g.sssp(0)
@@ -275,10 +287,10 @@ def test_grid_sizes_agree(dawn):
             assert np.array_equal(a, b), blocks
 
 
-def test_host_and_device_inputs_agree(dawn):
+def test_host_and_device_inputs_agree(dawn, Graph):
     wl = gg.rmat_u32(11, 8, nsrc=1, seed=9)
-    g1 = dawn.Graph(wl.row_ptr, wl.col, wl.weights)
-    g2 = dawn.Graph(torch.from_numpy(wl.row_ptr).cuda(), torch.from_numpy(wl.col).cuda(),
+    g1 = Graph(wl.row_ptr, wl.col, wl.weights)
+    g2 = Graph(torch.from_numpy(wl.row_ptr).cuda(), torch.from_numpy(wl.col).cuda(),
                     torch.from_numpy(wl.weights).cuda())
     s = int(wl.sources[0])
     for a, b in zip(solve(g1, s), solve(g2, s)):
@@ -293,6 +305,7 @@ def test_allocation_failure_reports_oom_and_handle_recovers(dawn):
     s = int(wl.sources[0])
     for nth in (1, 3, 5):
         g = dawn.Graph(wl.row_ptr, wl.col, wl.weights)
+        g.set_option(dawn.DAWN_OPT_SMALL_PATH, dawn.DAWN_SMALL_NEVER)  # the kernel with a device workspace
         g.set_option(dawn.DAWN_OPT_TEST_FAIL_ALLOC, nth)
         with pytest.raises(dawn.DawnError) as e:
             g.sssp(s)
@@ -300,6 +313,7 @@ def test_allocation_failure_reports_oom_and_handle_recovers(dawn):
         d, p, pe = solve(g, s)
         assert_exact(wl.row_ptr, wl.col, wl.weights, s, d, p, pe)
     g = dawn.Graph(wl.row_ptr, wl.col, wl.weights)
+    g.set_option(dawn.DAWN_OPT_SMALL_PATH, dawn.DAWN_SMALL_NEVER)
     g.set_option(dawn.DAWN_OPT_TEST_FAIL_ALLOC, 1)
     with pytest.raises(dawn.DawnError) as e:
         dawn.dawn_reserve(g.handle, 8)

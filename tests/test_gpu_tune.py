@@ -55,6 +55,7 @@ def workloads():
 def test_kernel_builds_exact(dawn, idx, ctas):
     name, rp, cl, w, srcs = workloads()[idx]
     g = dawn.Graph(rp, cl, w)
+    g.set_option(dawn.DAWN_OPT_SMALL_PATH, dawn.DAWN_SMALL_NEVER)  # the persistent kernel's builds
     g.set_option(dawn.DAWN_OPT_CTAS_PER_SM, ctas)
     for blocks in (0, 1, 5, 152):
         g.set_option(dawn.DAWN_OPT_GRID_BLOCKS, blocks)
@@ -76,6 +77,7 @@ def test_ctas_option_validated(dawn):
 def test_batch_sizes_agree(dawn, batch):
     wl = gg.rmat_u32(11, 8, nsrc=40, seed=24)
     g = dawn.Graph(wl.row_ptr, wl.col, wl.weights)
+    g.set_option(dawn.DAWN_OPT_SMALL_PATH, dawn.DAWN_SMALL_NEVER)  # batches of the persistent kernel
     g.set_option(dawn.DAWN_OPT_BATCH, batch)
     g.set_option(dawn.DAWN_OPT_CTAS_PER_SM, 4 if batch % 2 else 5)
     dist, par = g.msssp(wl.sources)
