@@ -76,35 +76,29 @@ __device__ __forceinline__ int32_t block_prefix(int32_t x, int32_t *sc, int32_t 
 
 // delta <- beta restricted to vertices with an out-edge; beta <- {}.  Returns
 // the new frontier size (block-uniform); adds its out-edges to *edges and the
-// marked vertices to *marks (thread-local partial sums).
+// marked vertices to *marks (thread-local partial sums).  Each thread owns a
+// contiguous range of vertices, so all threads share the work however few
+// bitmap words there are.
 __device__ int32_t small_build(int32_t n, const int32_t *rp, uint32_t *bm, int32_t *front, int32_t *sc,
                                unsigned long long *edges, unsigned long long *marks) {
-  const int32_t words = (n + 31) / 32;
+  const int32_t per = (n + (int32_t)blockDim.x - 1) / (int32_t)blockDim.x;
+  const int32_t v0 = (int32_t)threadIdx.x * per, v1 = min(v0 + per, n);
   int32_t mine = 0;
-  for (int32_t w = threadIdx.x; w < words; w += blockDim.x) {
-    uint32_t bits = bm[w];
-    *marks += __popc(bits);
-    while (bits) {
-      const int32_t v = w * 32 + __ffs(bits) - 1;
-      bits &= bits - 1;
-      const int32_t d = rp[v + 1] - rp[v];
-      if (d > 0) {
-        ++mine;
-        *edges += (unsigned long long)d;
-      }
+  for (int32_t v = v0; v < v1; ++v) {
+    if (!(bm[v >> 5] & (1u << (v & 31)))) continue;
+    ++*marks;
+    const int32_t d = rp[v + 1] - rp[v];
+    if (d > 0) {
+      ++mine;
+      *edges += (unsigned long long)d;
     }
   }
   int32_t total = 0;
   int32_t at = block_prefix(mine, sc, &total);
-  for (int32_t w = threadIdx.x; w < words; w += blockDim.x) {
-    uint32_t bits = bm[w];
-    bm[w] = 0u;
-    while (bits) {
-      const int32_t v = w * 32 + __ffs(bits) - 1;
-      bits &= bits - 1;
-      if (rp[v + 1] > rp[v]) front[at++] = v;
-    }
-  }
+  for (int32_t v = v0; v < v1; ++v)
+    if ((bm[v >> 5] & (1u << (v & 31))) && rp[v + 1] > rp[v]) front[at++] = v;
+  __syncthreads();  // every thread has read beta
+  for (int32_t w = threadIdx.x; w < (n + 31) / 32; w += blockDim.x) bm[w] = 0u;
   __syncthreads();
   return total;
 }
