@@ -48,6 +48,7 @@ __device__ __forceinline__ unsigned long long global_ns() {
 }
 
 constexpr int32_t kMark = 0x100;  // above every entry index of a tile (at most kTile)
+static_assert(kTile < kMark && kEdgesPerLane <= 4, "entry indices of a tile fit 8 bits, four per register");
 
 struct WarpTile {
   uint32_t ebase[kTile + 1];  // per entry: CSR index of its edge at virtual offset 0 (mod 2^32)
@@ -424,7 +425,7 @@ __device__ __forceinline__ void relax_tile(const GovmParams &p, WarpTile &wt, in
   // rounds).  Every load of a phase is issued before any result is used, so
   // the eight requests of a lane are in flight together.
   uint32_t eidx[kEdgesPerLane];
-  unsigned valid = 0;
+  unsigned valid = 0, jpack = 0;  // jpack: each round's owning entry (8 bits each), reused for the keys
   bool bad = false;
 #pragma unroll
   for (int r = 0; r < kEdgesPerLane; ++r) {
@@ -432,6 +433,7 @@ __device__ __forceinline__ void relax_tile(const GovmParams &p, WarpTile &wt, in
     eidx[r] = 0;
     if (x < xend) {
       const int32_t j = one ? 0 : wt.own[r * 32 + lane];
+      jpack |= (uint32_t)j << (8 * r);
       const uint32_t e = x + wt.ebase[j];
       if (e < (uint32_t)p.m) {
         valid |= 1u << r;
@@ -461,7 +463,7 @@ __device__ __forceinline__ void relax_tile(const GovmParams &p, WarpTile &wt, in
   unsigned need = 0;
 #pragma unroll
   for (int r = 0; r < kEdgesPerLane; ++r) {
-    ckey[r] = Key<WT>::add(wt.dkey[one ? 0 : wt.own[r * 32 + lane]], cw[r].y);
+    ckey[r] = Key<WT>::add(wt.dkey[(jpack >> (8 * r)) & 0xFFu], cw[r].y);
     const unsigned long long cand = ((unsigned long long)ckey[r] << 32) | eidx[r];
     if ((valid & (1u << r)) && cand < curst[r] && curst[r] != kSourceState) need |= 1u << r;
   }
