@@ -276,11 +276,13 @@ def run_sssp_bench(args, wl, device, world, rank):
 
 
 def run_e2e(args, wl, device, world, tuning=None):
-    """Same metric through the C ABI from pinned host buffers: per step the
-    graph is copied in and validated (dawn_create_graph with host inputs),
-    the tuned launch options are set, every source is solved, and each
-    source's dist + parent rows are copied back to pinned host memory,
-    overlapped with the following solves."""
+    """Same metric through the C ABI from pinned host buffers.  Every step
+    copies the graph in and validates it (dawn_create_graph with host
+    inputs), sets the tuned launch options, solves every source and copies
+    each source's dist + parent rows back to pinned host memory.  The steps
+    are pipelined the way a serving loop would run them: result copies go
+    back on a second stream while the next solves run, and the next step's
+    graph is uploaded on a third stream while this step's solves run."""
     import torch
     import paper_2306_07872_gb300 as dawn
 
@@ -296,37 +298,49 @@ def run_e2e(args, wl, device, world, tuning=None):
     par = torch.empty((S, wl.n), dtype=torch.int32, device=device)
     stream = torch.cuda.current_stream()
     copy_stream = torch.cuda.Stream(device=device)
+    ingest_stream = torch.cuda.Stream(device=device)
     done = [torch.cuda.Event() for _ in wl.sources]
     srcs = [int(s) for s in wl.sources]
 
-    def step():
-        h = dawn.dawn_create_graph(rp, cl, w, stream)
+    def ingest():
+        h = dawn.dawn_create_graph(rp, cl, w, ingest_stream)  # returns once the graph is validated
         if tuning:
             dawn.dawn_set_option(h, dawn.DAWN_OPT_CTAS_PER_SM, tuning["ctas_per_sm"])
             dawn.dawn_set_option(h, dawn.DAWN_OPT_GRID_BLOCKS, tuning["grid_blocks"])
+        return h
+
+    def solve(h):
+        stream.wait_stream(ingest_stream)  # the graph's device copy is complete
         for i, s in enumerate(srcs):
             dawn.dawn_sssp(h, s, dist[i], par[i], None, stream)
-            # each source's rows go back to the host on a second stream while
-            # the next solves run
             done[i].record(stream)
             copy_stream.wait_event(done[i])
             with torch.cuda.stream(copy_stream):
                 h_dist[i].copy_(dist[i], non_blocking=True)
                 h_par[i].copy_(par[i], non_blocking=True)
         stream.wait_stream(copy_stream)
-        code = dawn.dawn_status(h, True)
+
+    def finish(h):
+        code = dawn.dawn_status(h, True)  # waits for the solves and the copies back
         dawn.dawn_destroy(h)
         if code:
             raise dawn.DawnError(code, "e2e solve")
 
-    step()
+    def run(steps):
+        h = ingest()
+        for k in range(steps):
+            solve(h)
+            h_next = ingest() if k + 1 < steps else None  # overlaps this step's solves
+            finish(h)
+            h = h_next
+
+    run(1)  # warm-up
     torch.cuda.synchronize()
     steps = max(1, min(args.steps, 3))
     barrier(world)
     torch.cuda.synchronize()
     t = time.perf_counter()
-    for _ in range(steps):
-        step()
+    run(steps)
     torch.cuda.synchronize()
     el = time.perf_counter() - t
     barrier(world)
