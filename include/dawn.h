@@ -121,7 +121,8 @@ int dawn_set_weights(dawn_graph g, const void *weights, int flags, void *stream)
 /*
  * Pre-size the solver workspace for batches of up to k instances (optional;
  * solves grow it on demand).  Call before capturing solves into a CUDA
- * graph, since growing the workspace allocates device memory.
+ * graph, since growing the workspace allocates device memory.  (Solves by
+ * the small-graph kernel keep their state in shared memory and use none.)
  */
 int dawn_reserve(dawn_graph g, int32_t k);
 
@@ -131,8 +132,11 @@ int dawn_reserve(dawn_graph g, int32_t k);
  *   dist         device uint32[n] or float32[n] (per the graph's weight type)
  *   parent       device int32[n] or NULL
  *   parent_edge  device int32[n] or NULL
- * One persistent kernel performs initialisation, every GOVM step (with a
- * device-wide barrier and no host round trip per step) and the output.
+ * One kernel launch performs initialisation, every GOVM step and the output,
+ * with no host round trip per step: the persistent kernel (device-wide
+ * barriers between phases) or, for a graph whose solver state fits in one
+ * block's shared memory, the small-graph kernel (one block, block barriers;
+ * see DAWN_OPT_SMALL_PATH).
  */
 int dawn_sssp(dawn_graph g, int32_t source, void *dist, int32_t *parent, int32_t *parent_edge,
               void *stream);
@@ -147,8 +151,9 @@ int dawn_sssp(dawn_graph g, int32_t source, void *dist, int32_t *parent, int32_t
  *   k            number of instances, k >= 1
  *   dist         device [k][n] (row i holds the distances from sources[i])
  *   parent       device int32[k][n] or NULL
- * Large k is processed in chunks of instances, each chunk one persistent
- * launch.
+ * Large k is processed in chunks of instances (DAWN_OPT_BATCH), each chunk
+ * one launch: the persistent kernel, or the small-graph kernel with one block
+ * per instance.
  */
 int dawn_msssp(dawn_graph g, const int32_t *sources, int32_t k, void *dist, int32_t *parent,
                void *stream);
