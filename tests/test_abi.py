@@ -92,3 +92,53 @@ def test_tune_cache_keys_and_store(tmp_path):
     assert got[k1]["grid_blocks"] == 608 and got["other"]["grid_blocks"] == 0 and "candidates" not in got[k1]
     (tmp_path / "bad.json").write_text("not json")
     assert d.tune_cache_load(str(tmp_path / "bad.json")) == {}
+
+
+def test_host_argument_checks_reject_before_any_device_call(lib_path):
+    """Malformed sizes, a bad weight type, missing arrays and a NULL handle are
+    refused by the host-side checks of every entry point with
+    DAWN_ERR_INVALID; none of these paths reaches the CUDA runtime, so the
+    calls are safe without a GPU."""
+    import ctypes as C
+    import numpy as np
+    from paper_2306_07872_gb300 import dawn as d
+    lib = d.load_library(lib_path)
+    rp = np.array([0, 1, 1], dtype=np.int32)
+    col = np.array([1], dtype=np.int32)
+    w = np.array([3], dtype=np.uint32)
+    ptr = lambda a: a.ctypes.data_as(C.c_void_p)  # noqa: E731
+    out = C.c_void_p(12345)
+
+    def create(n, m, r=ptr(rp), c=ptr(col), wt=ptr(w), wtype=d.DAWN_W_U32):
+        out.value = 12345
+        rc = lib.dawn_create_graph(n, m, r, c, wt, wtype, 0, None, C.byref(out))
+        assert out.value is None, "a refused call must clear *out"
+        return rc
+
+    assert create(0, 1) == d.DAWN_ERR_INVALID                        # no vertices
+    assert create(-5, 1) == d.DAWN_ERR_INVALID
+    assert create(2, -1) == d.DAWN_ERR_INVALID                       # negative edge count
+    assert create(2, 1 << 31) == d.DAWN_ERR_INVALID                  # edge ids must fit int32
+    assert create(2, 1, r=None) == d.DAWN_ERR_INVALID                # missing row pointers
+    assert create(2, 1, c=None) == d.DAWN_ERR_INVALID                # missing columns with m > 0
+    assert create(2, 1, wt=None) == d.DAWN_ERR_INVALID               # missing weights with m > 0
+    assert create(2, 1, wtype=7) == d.DAWN_ERR_INVALID               # unknown weight type
+    assert lib.dawn_create_graph(2, 1, ptr(rp), ptr(col), ptr(w), 0, 0, None, None) == d.DAWN_ERR_INVALID
+
+    src = np.zeros(1, dtype=np.int32)
+    buf = np.zeros(4, dtype=np.float32)
+    INV = d.DAWN_ERR_INVALID
+    assert lib.dawn_set_weights(None, ptr(w), 0, None) == INV
+    assert lib.dawn_reserve(None, 1) == INV
+    assert lib.dawn_sssp(None, 0, ptr(buf), None, None, None) == INV
+    assert lib.dawn_msssp(None, ptr(src), 1, ptr(buf), None, None) == INV
+    assert lib.dawn_sssp_roots(None, ptr(src), 1, ptr(buf), None, None, None) == INV
+    assert lib.dawn_sssp_backward(None, ptr(src), ptr(buf), ptr(buf), None) == INV
+    assert lib.dawn_sssp_noalloc(None, 0, ptr(buf), None, None, None, None) == INV
+    assert lib.dawn_status(None, 0) == INV
+    assert lib.dawn_get_stats(None, None) == INV
+    assert lib.dawn_set_option(None, d.DAWN_OPT_BATCH, 1) == INV
+    assert lib.dawn_get_trace(None, None, 0) == -INV
+    assert lib.dawn_graph_info(None, None, None, None) == INV
+    assert lib.dawn_autotune(None, d.DAWN_TUNE_SSSP, ptr(src), 1, 1, None, None) == INV
+    lib.dawn_destroy(None)  # a NULL handle is a no-op
