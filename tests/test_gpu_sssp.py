@@ -168,6 +168,39 @@ def test_hub_rows_span_many_tiles(dawn, Graph):
     assert_exact(rp, cl, w, 0, d, p, pe)
 
 
+def test_hub_lowered_in_every_step(dawn, Graph):
+    # A hub of 6000 out-edges (47 tiles) is reached first by a heavy edge and
+    # then, one step later each time, by paths with more hops and less
+    # weight, so it is lowered in every step while its own tiles are being
+    # expanded: tiles of one step may read different keys.  A vertex is left
+    # out of the next frontier only when every tile used its current key.
+    L, fan = 30, 6000
+    n = 2 + L + fan + 1
+    hub, sink = 1, n - 1
+    edges, ws = [], []
+    chain = list(range(2, 2 + L))
+    prev = 0
+    for i, a in enumerate(chain):
+        edges.append((prev, a)); ws.append(1)
+        edges.append((a, hub)); ws.append(5000 - 150 * i)
+        prev = a
+    edges.append((0, hub)); ws.append(6000)
+    leaves = range(2 + L, 2 + L + fan)
+    for j, v in enumerate(leaves):
+        edges.append((hub, v)); ws.append(1 + (j * 7919) % 251)
+        if j % 3 == 0:
+            edges.append((v, sink)); ws.append(1 + j % 13)
+        if j % 5 == 0 and j + 1 < fan:
+            edges.append((v, v + 1)); ws.append(2)
+    rp, cl, w = gg.csr_from_edges(n, edges, ws)
+    g = Graph(rp, cl, w)
+    for s in (0, 2, 2 + L // 2):
+        assert_exact(rp, cl, w, s, *solve(g, s))
+    wf = w.astype(np.float32) * np.float32(0.37)
+    g = Graph(rp, cl, wf)
+    assert_exact(rp, cl, wf, 0, *solve(g, 0))
+
+
 def test_many_degree_one_frontier(dawn, Graph):
     # binary tree (frontier of many out-degree-1/2 vertices: up to 257 entries per tile)
     n = 1 << 15
