@@ -13,7 +13,9 @@
  *
  * Conventions shared by every entry point
  * ---------------------------------------
- *  - Every function returns a dawn_status_code value; nothing throws across the ABI.
+ *  - Every function returns a dawn_status_code value, except dawn_get_trace
+ *    (a row count, or a negated code), dawn_status_string and dawn_destroy;
+ *    nothing throws across the ABI.
  *  - Arguments checked on the host (sizes, pointers, scalar ids) fail
  *    synchronously.  Arguments that live in device memory (source / root
  *    arrays) are checked by the kernel, which then skips the solve and leaves
