@@ -527,19 +527,19 @@ def run_mu(args):
     """The paper's validation experiment (Section 4.2) on synthetic graphs:
     every graph is solved with all weights 1.0f and with fp32 weights
     uniform in [0, 2]; mu = path updates / (reached vertices - 1) on the GPU
-    (vertices entering beta per step) and, for one source, from the literal
-    Algorithm 2 in the oracle.  With unit weights mu is exactly 1; the
-    difference is the share of paths that GOVM had to update."""
+    (vertices entering beta per step).  With unit weights mu is exactly 1;
+    the difference is the share of paths that GOVM had to update.  Unless
+    --no-cpu is given, the line's cpu_baseline holds mu of the literal
+    Algorithm 2 (the oracle) for the first source of each graph."""
     import torch
     import graphgen as gg
-    import oracle
     import paper_2306_07872_gb300 as dawn
     graphs = {
         "rmat_s18": lambda: gg.rmat(18, 16, seed=0, relabel=True),
         "er_n262144_d16": lambda: gg.erdos_renyi(1 << 18, 16 << 18, seed=3),
         "grid_512": lambda: gg.grid(512, 0.01, seed=1)[:2],
     }
-    out = {}
+    out, cases = {}, []
     for name, make in graphs.items():
         rp, cl = make()
         src, _, e_wcc = gg.wcc_sources(rp, cl, 4, seed=5)
@@ -555,13 +555,33 @@ def run_mu(args):
                 reached = int(torch.isfinite(dist).sum().item())
                 mus.append(st["updates"] / max(reached - 1, 1))
                 times.append(t)
-            _, ost = oracle.govm(rp, cl, w, int(src[0]))
-            res[wname] = {"mu_gpu": float(np.mean(mus)), "mu_oracle_alg2": ost["mu"], "solve_ms": 1e3 * float(np.mean(times))}
+            res[wname] = {"mu_gpu": float(np.mean(mus)), "solve_ms": 1e3 * float(np.mean(times))}
+            cases.append((name, wname, rp, cl, w, int(src[0])))
             g.close()
         res["updated_path_ratio_gpu"] = res["u02"]["mu_gpu"] - 1.0
-        res["updated_path_ratio_oracle"] = res["u02"]["mu_oracle_alg2"] - 1.0
         res["time_ratio_u02_over_unit"] = res["u02"]["solve_ms"] / res["unit"]["solve_ms"]
         out[name] = res
+    if not args.no_cpu:
+        out["cpu_baseline"] = cpu_baseline_mu(cases)
+    return out
+
+
+def cpu_baseline_mu(cases):
+    """CPU leg of the mu experiment: the oracle's literal Algorithm 2 (one
+    thread, in-place alpha) on each (graph, weights, source) case, giving its
+    own mu and time.  Algorithm 2 updates alpha in place and the GPU reads it
+    in place across concurrent tiles, so the two mu values differ; only the
+    fixpoint is shared."""
+    import oracle
+    out = {"kind": "oracle", "cores": 1, "sample": "first WCC source of each graph and weight set, literal "
+           "GOVM (Algorithm 2), one thread"}
+    for name, wname, rp, cl, w, s in cases:
+        t0 = time.perf_counter()
+        _, ost = oracle.govm(rp, cl, w, s)
+        out.setdefault(name, {})[wname] = {"mu_oracle_alg2": ost["mu"],
+                                           "solve_ms": (time.perf_counter() - t0) * 1e3}
+    for name in {c[0] for c in cases}:
+        out[name]["updated_path_ratio_oracle"] = out[name]["u02"]["mu_oracle_alg2"] - 1.0
     return out
 
 
