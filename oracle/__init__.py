@@ -14,6 +14,10 @@ plus three pure-Python / numpy routines kept here for independence:
 * :func:`fd_grad` -- central finite differences of L = sum c_t dist[t] with
   float64 Dijkstra.
 
+Parity unpinned: the work counters that :func:`govm` and :func:`gsvm` return
+(steps, edges scanned, updates, mu) beyond mu = 1 on unit weights; the
+distances, parents and gradients are pinned by the tests.
+
 Conventions shared with the library under test: unreachable distance is
 0xFFFFFFFF for uint32 weights and +inf for float32 weights; parent[v] is the
 tail of v's parent edge, parent[root] = root, parent[unreachable] = -1.

@@ -32,6 +32,13 @@
  *     guard skips every root (single-source SSSP is the case k = 1);
  *   - the loop is capped at n steps as in both algorithms (while step < n);
  *     a run that reaches the cap reports "not converged".
+ *
+ * Parity unpinned: the work counters of govm_* / gsvm_* (steps, edges
+ * scanned, path updates and so mu = updates / (reached - 1)).  Only mu = 1
+ * and one step per BFS level on unit weights are pinned; the paper's own mu
+ * values (Section 4.2) were measured on graphs that are not available, and
+ * the counters depend on the in-place update order, which the paper leaves
+ * open.  Distances, parents and gradients are pinned (tests/test_oracle.py).
  */
 #include <math.h>
 #include <stdint.h>
