@@ -155,6 +155,18 @@ def test_fp32_left_fold_rounding(alg):
     assert oracle.brute_force(rp, cl, w, 0)[3] == t24
 
 
+@pytest.mark.parametrize("alg", ("govm", "gsvm"))
+def test_fp32_candidate_rounding_to_current_distance_is_no_update(alg):
+    # 0->2 (2^24), 0->1 (0.5), 1->2 (2^24 - 1).  The path through 1 sums to
+    # 2^24 - 0.5 exactly, which rounds (ties to even) to 2^24 = dist[2]: in
+    # fp32 it is not an improvement, so the run makes exactly two updates
+    # (vertices 1 and 2 in step 1) and stops after step 2.
+    rp, cl, w = gg.csr_from_edges(3, [(0, 2), (0, 1), (1, 2)], [2.0 ** 24, 0.5, 2.0 ** 24 - 1], np.float32)
+    d, st = oracle.govm(rp, cl, w, 0, algorithm=alg)
+    assert d.tolist() == [0.0, 0.5, 2.0 ** 24]
+    assert st["updates"] == 2 and st["steps"] == 2 and st["converged"] == 1
+
+
 @pytest.mark.parametrize("seed", range(30))
 def test_fp32_brute_force_small(seed):
     # random fp32 weights (not dyadic): exact min over simple paths of the
@@ -258,6 +270,12 @@ def test_unit_weights_are_bfs_levels_and_mu_is_one(seed):
     assert st["updates"] == st["reached"] - 1 and st["multi_updated"] == 0 and st["mu"] == 1.0
     # one step per BFS level plus the final step that changes nothing
     assert st["steps"] == int(levels[np.isfinite(levels)].max()) + 1
+    # each reached vertex enters delta exactly once (at its own level), so the
+    # work counters are closed forms: its out-edges are scanned once
+    outdeg = np.diff(wl.row_ptr)
+    fin = np.isfinite(levels)
+    assert st["edges_scanned"] == int(outdeg[fin].sum())
+    assert st["frontier_sum"] == int((outdeg[fin] > 0).sum())
     # with weights in [1, 255] paths do change: mu > 1
     wl2 = gg.rmat_u32(12, 8, nsrc=1, seed=seed)
     _, st2 = oracle.govm(wl2.row_ptr, wl2.col, wl2.weights, s)
@@ -290,6 +308,24 @@ def test_parent_rule_lowest_edge_index():
     assert d.tolist() == [0, 2, 1] and pe.tolist() == [-1, 0, 1]
     p = oracle.parent_vertices(rp, 0, d, pe, "u32")
     assert p.tolist() == [0, 0, 0]
+
+
+def test_parent_rule_fp32_needs_exact_equality():
+    # 0->1 (1), 0->2 (1), 1->3 (100 + 2^-17), 2->3 (100).  dist[3] = 101 via
+    # vertex 2; the lower-indexed edge from 1 offers 101 + 2^-17, one ulp
+    # above, so it is not tight and not the parent; the certificate rejects
+    # it as a parent edge (code 3).
+    w13 = np.nextafter(np.float32(100), np.float32(200))
+    assert float(w13) == 100 + 2.0 ** -17
+    rp, cl, w = gg.csr_from_edges(4, [(0, 1), (0, 2), (1, 3), (2, 3)], [1, 1, w13, 100], np.float32)
+    d = oracle.dijkstra(rp, cl, w, 0)
+    assert d.tolist() == [0, 1, 1, 101]
+    pe = oracle.parent_edges(rp, cl, w, 0, d)
+    assert pe.tolist() == [-1, 0, 1, 3]
+    assert oracle.certificate(rp, cl, w, 0, d, pe) == (0, -1)
+    bad = pe.copy()
+    bad[3] = 2
+    assert oracle.certificate(rp, cl, w, 0, d, bad) == (3, 3)
 
 
 def test_zero_weight_tie_can_make_parent_cycle():
@@ -339,6 +375,49 @@ def test_certificate_accepts_oracle_and_rejects_planted_mistakes(kind):
     d_t = oracle.dijkstra(rp_t, cl_t, w_t, 0)
     pe_t = oracle.parent_edges(rp, cl, w, 0, d_t)
     assert oracle.certificate(rp, cl, w, 0, d_t, pe_t)[0] != 0
+
+
+@pytest.mark.parametrize("kind", ["u32", "f32"])
+def test_certificate_rejects_a_consistent_tree_that_misses_a_shorter_edge(kind):
+    # Solve on the graph without one tree edge e*: the result is a valid
+    # tree with tight parent edges in the full graph too, but e* offers a
+    # shorter path, which only the edge check (code 2) can see.
+    if kind == "u32":
+        rp, cl, w = gg.random_small(200, 1500, 21, kind="u32", wlo=1, whi=40)
+    else:
+        rp, cl, w = gg.random_small(200, 1500, 21, kind="f32", wlo=0.5, whi=2.0)
+    d = oracle.dijkstra(rp, cl, w, 0)
+    pe = oracle.parent_edges(rp, cl, w, 0, d)
+    tails = oracle.edge_tails(rp)
+    for e_star in sorted(int(e) for e in pe[pe >= 0]):
+        keep = np.ones(len(cl), bool)
+        keep[e_star] = False
+        rp2, cl2, w2 = gg.csr_from_edges(200, np.stack([tails[keep], cl[keep]], 1), w[keep], w.dtype)
+        d2 = oracle.dijkstra(rp2, cl2, w2, 0)
+        if np.array_equal(d2, d):
+            continue  # an equally short path remains
+        pe2 = oracle.parent_edges(rp2, cl2, w2, 0, d2)
+        full = np.nonzero(keep)[0]  # edge index in the reduced graph -> index in the full graph
+        pe2_full = np.where(pe2 >= 0, full[np.maximum(pe2, 0)], -1).astype(np.int32)
+        assert oracle.certificate(rp2, cl2, w2, 0, d2, pe2)[0] == 0
+        code, where = oracle.certificate(rp, cl, w, 0, d2, pe2_full)
+        assert code == 2
+        assert (d2[tails[where]] + w[where]) < d2[cl[where]]
+        return
+    pytest.fail("no tree edge whose removal lengthens a path")
+
+
+@pytest.mark.parametrize("kind", ["u32", "f32"])
+def test_certificate_rejects_a_parent_edge_on_an_unreachable_vertex(kind):
+    # 0->1; vertex 2 is reached only from the unreachable vertex 3 (edge 3->2)
+    rp, cl, w = gg.csr_from_edges(4, [(0, 1), (3, 2)], [1, 1], np.uint32 if kind == "u32" else np.float32)
+    d = oracle.dijkstra(rp, cl, w, 0)
+    pe = oracle.parent_edges(rp, cl, w, 0, d)
+    assert pe.tolist() == [-1, 0, -1, -1]
+    assert oracle.certificate(rp, cl, w, 0, d, pe) == (0, -1)
+    bad = pe.copy()
+    bad[2] = 1
+    assert oracle.certificate(rp, cl, w, 0, d, bad) == (4, 2)
 
 
 def test_certificate_on_workload_sources():
@@ -471,3 +550,28 @@ def test_negative_cycle_reported():
     assert oracle.bellman_ford(rp, cl, w, 3)[1] is False
     d3, st3 = oracle.govm(rp, cl, w, 3)
     assert st3["converged"] == 1 and d3.tolist() == [int(oracle.I32_INF)] * 3 + [0]
+
+
+def test_negative_cycle_through_the_source_is_excluded_by_the_guard():
+    # 0->1 (1), 1->0 (-5), 1->2 (2): the cycle 0->1->0 has length -4 but only
+    # re-enters the source, whose distance the "index != source" guard keeps
+    # at 0 (Algorithm 2); so dist = [0, 1, 3] and the run converges.
+    rp, cl, w = gg.csr_from_edges(3, [(0, 1), (1, 0), (1, 2)], np.array([1, -5, 2], np.int32), np.int32)
+    d, st = oracle.govm(rp, cl, w, 0)
+    assert d.tolist() == [0, 1, 3] and st["converged"] == 1 and st["updates"] == 2
+    d_bf, neg = oracle.bellman_ford(rp, cl, w, 0)
+    assert not neg and d_bf.tolist() == [0, 1, 3]
+
+
+def test_bellman_ford_path_against_csr_order_needs_n_minus_1_rounds():
+    # edges i+1 -> i, source n-1: a round visits tails in increasing order, so
+    # each round extends the known path by one edge and the last vertex needs
+    # all n - 1 rounds; dist[i] is the suffix sum of the weights.
+    ws = np.array([3, -1, 4, 1, -5, 9, 2], np.int32)
+    n = len(ws) + 1
+    rp, cl, w = gg.csr_from_edges(n, [(i + 1, i) for i in range(n - 1)], ws, np.int32)
+    expect = [int(ws[i:].sum()) for i in range(n - 1)] + [0]
+    d_bf, neg = oracle.bellman_ford(rp, cl, w, n - 1)
+    assert not neg and d_bf.tolist() == expect
+    d, st = oracle.govm(rp, cl, w, n - 1)
+    assert d.tolist() == expect and st["steps"] == n
