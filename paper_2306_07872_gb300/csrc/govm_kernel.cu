@@ -485,9 +485,9 @@ __device__ __forceinline__ void relax_tile(const GovmParams &p, WarpTile &wt, in
 }
 
 // MINB = CTAs per SM the build targets: 5 caps a thread at 48 registers
-// (40 resident warps per SM, the most latency hiding), 4 at 64 (no spills,
-// more loads in flight per warp).  Which is faster depends on the graph;
-// dawn_autotune picks it.
+// (40 resident warps per SM, the most latency hiding), 4 at 64 (more loads in
+// flight per warp).  Both spill a few dozen bytes, mostly in the frontier
+// build (ptxas -v).  Which is faster depends on the graph; dawn_autotune picks.
 template <int WT, int MINB>
 __global__ void __launch_bounds__(kBlockThreads, MINB) govm_kernel(GovmParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
