@@ -173,6 +173,20 @@ def bytes_alg(st):
     return 16 * st["frontier_sum"] + 12 * st["edges_scanned"] + 12 * st["updates"]
 
 
+def roofline_entry(b_alg: float, seconds: float, kernel: str, rule: str):
+    """Algorithmic bytes per call over the call's CUDA-event time, against
+    the measured HBM copy bandwidth."""
+    peak, kind = measured_peak()
+    gbs = b_alg / seconds / 1e9
+    return {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+            "peak_kind": f"{kind} copy bandwidth", "kernel": kernel, "b_alg_per_call": b_alg, "b_alg_rule": rule}
+
+
+def host_threads(units: int) -> int:
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    return max(1, min(cores, 16, units))
+
+
 # --------------------------------------------------------------- our solver
 
 def run_sssp_bench(args, wl, device, world, rank):
@@ -425,7 +439,8 @@ def run_batched(args):
     tune_batch = None if args.no_tune else g.autotune(wl.sources, mode="msssp", reps=2)
     t_batch = _time(lambda: dawn.dawn_msssp(g.handle, src, dist, par))
     g.check()
-    st = g.stats()
+    st = g.stats()  # summed over the launches of the last call
+    rows_host = dist[:64].cpu().numpy()
     srcs = [int(x) for x in wl.sources]
     # the loop arm gets its own tuned launch shape
     tune_loop = None if args.no_tune else g.autotune(wl.sources[:8], mode="sssp", reps=2)
@@ -439,7 +454,12 @@ def run_batched(args):
                                 "gteps_loop": k * wl.e_wcc / t_loop / 1e9,
                                 "edges_scanned_per_instance": st["edges_scanned"] / k,
                                 "updates_per_instance": st["updates"] / k,
-                                "tuning_batched": tune_batch, "tuning_loop": tune_loop}
+                                "tuning_batched": tune_batch, "tuning_loop": tune_loop,
+                                "roofline": roofline_entry(bytes_alg(st), t_batch, "govm_kernel (1024 instances)",
+                                                           "16 B per frontier vertex + 12 B per scanned edge + "
+                                                           "12 B per update, summed over the instances")}
+    if not args.no_cpu:
+        out["msssp_rmat18_1024"]["cpu_baseline"] = cpu_leg_sources(wl, rows_host, args.cpu_budget)
     del dist, par
     g.close()
     torch.cuda.empty_cache()
@@ -451,6 +471,7 @@ def run_batched(args):
     tune_roots = None if args.no_tune else gu.autotune(wb.sources, mode="roots", reps=2)
     t_roots = _time(lambda: dawn.dawn_sssp_roots(gu.handle, roots, du, pu))
     gu.check()
+    st_roots = gu.stats()
     offs = wb.extra["offsets"]
     parts = []
     for i in range(64):
@@ -470,7 +491,12 @@ def run_batched(args):
         p_.check()
     out["roots_er64"] = {"one_launch_s": t_roots, "loop_s": t_loop2, "speedup": t_loop2 / t_roots,
                          "gteps_one_launch": wb.m / t_roots / 1e9, "gteps_loop": wb.m / t_loop2 / 1e9,
-                         "n": wb.n, "m": wb.m, "tuning_one_launch": tune_roots}
+                         "n": wb.n, "m": wb.m, "tuning_one_launch": tune_roots,
+                         "roofline": roofline_entry(bytes_alg(st_roots), t_roots, "govm_kernel (multi-root forest)",
+                                                    "16 B per frontier vertex + 12 B per scanned edge + "
+                                                    "12 B per update")}
+    if not args.no_cpu:
+        out["roots_er64"]["cpu_baseline"] = cpu_leg_roots(wb, du.cpu().numpy())
     for p_ in parts:
         p_.close()
     gu.close()
@@ -515,12 +541,68 @@ def run_diff(args):
     t_cfb = _time(c_abi_fwd_bwd, reps=20, warm=3)
     g.check()
     g.close()
-    return {"diff_rmat16_f32": {"plain_sssp_s": t_plain, "c_abi_forward_backward_s": t_cfb,
+    tree = int((pe >= 0).sum().item())
+    b_bw = 8 * wl.n + 4 * wl.m + 12 * tree
+    res = {"diff_rmat16_f32": {"plain_sssp_s": t_plain, "c_abi_forward_backward_s": t_cfb,
                                 "c_abi_fb_over_plain": t_cfb / t_plain, "backward_kernel_s": t_bwd,
                                 "autograd_forward_s": t_fwd, "autograd_forward_backward_s": t_fb,
                                 "autograd_fb_over_plain": t_fb / t_plain,
                                 "autograd_forward_backward_nosync_s": t_fb_ns,
-                                "autograd_fb_nosync_over_plain": t_fb_ns / t_plain, "n": wl.n, "m": wl.m}}
+                                "autograd_fb_nosync_over_plain": t_fb_ns / t_plain, "n": wl.n, "m": wl.m,
+                                "tree_edges": tree,
+                                "roofline_backward": roofline_entry(
+                                    b_bw, t_bwd, "bw_count_kernel + bw_walk_kernel",
+                                    "8 B per vertex (dL/d dist, parent edge) + 4 B per edge (dL/dw written, "
+                                    "zeros included) + 12 B per tree edge (tail lookup, accumulator "
+                                    "read-modify-write)")}}
+    if not args.no_cpu:
+        res["diff_rmat16_f32"]["cpu_baseline"] = cpu_leg_diff(wl, grad_dist.cpu().numpy(), grad_w.cpu().numpy())
+    return res
+
+
+def cpu_leg_sources(wl, gpu_rows, budget_s: float):
+    """Oracle beside the batched solve: literal Algorithm 2, one source per
+    host thread, on a bounded prefix of the sources; the first rows are
+    compared bit for bit with the GPU's."""
+    import oracle
+    threads = host_threads(len(wl.sources))
+    t1, _ = oracle.timed_govm(wl.row_ptr, wl.col, wl.weights, [int(wl.sources[0])], threads=1)
+    nsrc = min(len(wl.sources), threads * max(1, int(budget_s / max(t1, 1e-3) / 2)))
+    sample = [int(x) for x in wl.sources[:nsrc]]
+    el, res = oracle.timed_govm(wl.row_ptr, wl.col, wl.weights, sample, threads=threads)
+    same = [np.array_equal(np.asarray(r[0]).view(np.uint32), gpu_rows[i].view(np.uint32))
+            for i, r in enumerate(res[:len(gpu_rows)])]
+    return {"value": len(sample) * wl.e_wcc / el / 1e9, "unit": "GTEPS", "cores": threads, "kind": "oracle",
+            "sample": f"{len(sample)} of the {len(wl.sources)} sources, literal GOVM (Algorithm 2), one source per "
+                      f"thread, {el:.1f} s",
+            "bit_exact_vs_gpu": {"rows_compared": len(same), "all_equal": bool(all(same))}}
+
+
+def cpu_leg_roots(wb, gpu_dist):
+    """Oracle beside the multi-root solve: literal Algorithm 2 with all roots
+    at once (one thread), compared bit for bit with the GPU."""
+    import oracle
+    t0 = time.perf_counter()
+    d, _ = oracle.govm(wb.row_ptr, wb.col, wb.weights, wb.sources)
+    el = time.perf_counter() - t0
+    return {"value": wb.m / el / 1e9, "unit": "GTEPS", "cores": 1, "kind": "oracle",
+            "sample": f"the whole forest ({len(wb.sources)} roots), literal GOVM (Algorithm 2), one thread, "
+                      f"{el:.2f} s",
+            "bit_exact_vs_gpu": bool(np.array_equal(np.asarray(d).view(np.uint32), gpu_dist.view(np.uint32)))}
+
+
+def cpu_leg_diff(wl, c, gpu_grad):
+    """Oracle beside forward + backward: fp32 Dijkstra, the parent rule and
+    the float64 subtree gradient (one thread); the GPU gradient's largest
+    error relative to the largest reference value is reported."""
+    import oracle
+    t0 = time.perf_counter()
+    g_ref = oracle.subtree_grad(wl.row_ptr, wl.col, wl.weights, 0, c)
+    el = time.perf_counter() - t0
+    scale = float(np.max(np.abs(g_ref))) or 1.0
+    return {"seconds": el, "cores": 1, "kind": "oracle",
+            "sample": "the whole graph: fp32 Dijkstra, lowest-index parents, float64 Dijkstra and subtree sums",
+            "max_abs_err_over_max_ref": float(np.max(np.abs(gpu_grad.astype(np.float64) - g_ref))) / scale}
 
 
 def run_mu(args):
