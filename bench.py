@@ -686,11 +686,23 @@ def run_apsp(args):
     tuning = None if args.no_tune else g.autotune(np.arange(n, dtype=np.int32), mode="msssp", reps=1)
     t = _time(lambda: dawn.dawn_msssp(g.handle, src, dist, None), reps=2, warm=1)
     g.check()
-    scanned = g.stats()["edges_scanned"]  # summed over all launches of the call
+    st = g.stats()  # summed over all launches of the call
+    scanned = st["edges_scanned"]
     g.close()
+    small = bool(tuning) and tuning.get("small_path") == dawn.DAWN_SMALL_WHEN_STATE_FITS
+    if small:  # state, bitmap and frontier live in shared memory: only the CSR and the output cross the SM
+        b_dev = 8 * st["frontier_sum"] + 8 * scanned + 4 * n * n
+        rule = ("small-graph kernel: 8 B per frontier vertex (row_ptr pair) + 8 B per scanned edge (column and "
+                "weight) + 4 B of dist per vertex and source; the solver state stays in shared memory and the "
+                "2.2 MB CSR in L2, so HBM is not the bound")
+    else:
+        b_dev = bytes_alg(st)
+        rule = "16 B per frontier vertex + 12 B per scanned edge + 12 B per update, summed over the sources"
     return {"apsp_rmat14": {"n": n, "m": len(cl), "s_wcc": s_wcc, "e_wcc": e_wcc, "seconds": t,
                             "gteps": n * e_wcc / t / 1e9, "edges_scanned": scanned,
-                            "mu_work": scanned / (s_wcc * e_wcc), "tuning": tuning}}
+                            "mu_work": scanned / (s_wcc * e_wcc), "tuning": tuning,
+                            "roofline": roofline_entry(b_dev, t, "govm_small_kernel" if small else "govm_kernel",
+                                                       rule)}}
 
 
 def run_gsvm(args):
