@@ -1,0 +1,72 @@
+"""Host logic of bench.py on CPU (no GPU): the reference arm's JSON line,
+the algorithmic-byte and roofline arithmetic, the lookup of committed ncu
+traffic by kernel-source hash, and the oracle legs that sit beside the GPU
+results."""
+import json
+import os
+import subprocess
+import sys
+
+import numpy as np
+import pytest
+
+import bench
+import graphgen as gg
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_reference_arm_prints_the_contract_line():
+    p = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--workload", "tiny", "--steps", "2",
+                        "--warmup", "3"], cwd=ROOT, stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True,
+                       timeout=300)
+    assert p.returncode == 0, p.stderr[-2000:]
+    lines = [l for l in p.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    line = json.loads(lines[0])
+    assert line["impl"] == "reference" and line["unit"] == "GTEPS" and line["higher_is_better"] is True
+    assert line["metric"] == bench.METRIC and line["steps"] == 2 and line["warmup"] == 3
+    assert line["value"] > 0 and line["cpu_baseline"]["value"] == line["value"]
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"] == {"value": line["value"], "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert line["config"]["workload"] == gg.tiny_er().name
+
+
+def test_bytes_alg_and_roofline_arithmetic():
+    st = {"frontier_sum": 10, "edges_scanned": 100, "updates": 7}
+    assert bench.bytes_alg(st) == 16 * 10 + 12 * 100 + 12 * 7
+    r = bench.roofline_entry(2e9, 1e-3, "k", "rule")
+    peak, kind = bench.measured_peak()
+    assert r["achieved"] == pytest.approx(2000.0) and r["peak"] == peak
+    assert r["frac"] == pytest.approx(2000.0 / peak) and r["unit"] == "GB/s" and kind in r["peak_kind"]
+
+
+def test_recorded_traffic_follows_the_kernel_source_hash(monkeypatch):
+    # the committed summaries were taken on the current kernel sources
+    assert bench.recorded_traffic("rmat_s22_ef16_u32") == pytest.approx(2.0186e9)
+    assert bench.recorded_traffic("grid_2048x2048_f32") == pytest.approx(9.1537e9)
+    assert bench.recorded_traffic("no_such_workload") is None
+    # once the kernel changes, the old counters no longer apply
+    monkeypatch.setattr(bench, "kernel_hash", lambda: "0123456789abcdef")
+    assert bench.recorded_traffic("rmat_s22_ef16_u32") is None
+
+
+def test_oracle_legs_beside_batched_and_backward_results():
+    wl = gg.rmat_u32(11, 16, nsrc=16, seed=1)
+    rows = np.stack([oracle.dijkstra(wl.row_ptr, wl.col, wl.weights, int(s)) for s in wl.sources[:4]])
+    out = bench.cpu_leg_sources(wl, rows, 0.5)
+    assert out["bit_exact_vs_gpu"] == {"rows_compared": 4, "all_equal": True}
+    bad = rows.copy()
+    bad[2, int(np.argmax(bad[2] != 0xFFFFFFFF))] ^= 1  # one flipped bit in a reached distance
+    assert bench.cpu_leg_sources(wl, bad, 0.5)["bit_exact_vs_gpu"]["all_equal"] is False
+
+    wb = gg.er_batch(count=4, nlo=100, nhi=800, dlo=2, dhi=6, seed=2)
+    d = oracle.dijkstra(wb.row_ptr, wb.col, wb.weights, wb.sources)
+    assert bench.cpu_leg_roots(wb, d)["bit_exact_vs_gpu"] is True
+
+    wd = gg.rmat_f32_diff(scale=9, edge_factor=8, ntargets=16, seed=0)
+    c = np.zeros(wd.n, np.float32)
+    c[wd.extra["targets"]] = wd.extra["coef"]
+    g = oracle.subtree_grad(wd.row_ptr, wd.col, wd.weights, 0, c).astype(np.float32)
+    assert bench.cpu_leg_diff(wd, c, g)["max_abs_err_over_max_ref"] < 1e-6
