@@ -494,7 +494,7 @@ int parents_f32(int32_t n, const int32_t *row_ptr, const int32_t *col, const flo
  * walk (the tree path) and a lower bound on every walk (fl(+) is monotone),
  * and that infinite dist coincides with unreachability.
  */
-static int cert_tree(int32_t n, const int32_t *row_ptr, const int32_t *col, const uint8_t *is_root,
+static int cert_tree(int32_t n, const int32_t *row_ptr, const uint8_t *is_root,
                      const uint8_t *finite, const int32_t *parent_edge, int64_t *where) {
   /* tail of each parent edge by binary search in row_ptr */
   uint8_t *state = (uint8_t *)calloc((size_t)n, 1); /* 0 new, 1 on path, 2 done */
@@ -546,7 +546,7 @@ int cert_u32(int32_t n, const int32_t *row_ptr, const int32_t *col, const uint32
     while (hi - lo > 1) { int32_t mid = lo + (hi - lo) / 2; if (row_ptr[mid] <= e) lo = mid; else hi = mid; }
     if (!finite[lo] || dist[lo] + w[e] != dist[v]) { rc = 3; *where = v; }
   }
-  if (!rc) rc = cert_tree(n, row_ptr, col, is_root, finite, parent_edge, where);
+  if (!rc) rc = cert_tree(n, row_ptr, is_root, finite, parent_edge, where);
   free(is_root); free(finite);
   return rc;
 }
@@ -578,7 +578,7 @@ int cert_f32(int32_t n, const int32_t *row_ptr, const int32_t *col, const float 
     float s = dist[lo] + w[e];
     if (!finite[lo] || s != dist[v]) { rc = 3; *where = v; }
   }
-  if (!rc) rc = cert_tree(n, row_ptr, col, is_root, finite, parent_edge, where);
+  if (!rc) rc = cert_tree(n, row_ptr, is_root, finite, parent_edge, where);
   free(is_root); free(finite);
   return rc;
 }
@@ -738,7 +738,7 @@ int cert_i32(int32_t n, const int32_t *row_ptr, const int32_t *col, const int32_
     while (hi - lo > 1) { int32_t mid = lo + (hi - lo) / 2; if (row_ptr[mid] <= e) lo = mid; else hi = mid; }
     if (!finite[lo] || dist[lo] + w[e] != dist[v]) { rc = 3; *where = v; }
   }
-  if (!rc) rc = cert_tree(n, row_ptr, col, is_root, finite, parent_edge, where);
+  if (!rc) rc = cert_tree(n, row_ptr, is_root, finite, parent_edge, where);
   free(is_root); free(finite);
   return rc;
 }
