@@ -67,6 +67,31 @@ def test_path_graph_prefix_sums(alg):
     assert d.tolist() == [0] + list(np.cumsum(ws))
 
 
+def test_path_graph_step_and_work_counts():
+    # 0 -> 1 -> ... -> 9.  Algorithm 2 expands one new vertex per step (9
+    # steps that change a path, then one that changes nothing): 9 edges
+    # scanned, 9 updates.  Algorithm 1 sweeps the reached vertices in id
+    # order with alpha updated in place, so its first sweep reaches the whole
+    # path and its second changes nothing: 2 steps, 9 + 9 edges scanned.
+    ws = [3, 1, 4, 1, 5, 9, 2, 6, 5]
+    rp, cl, w = gg.csr_from_edges(10, [(i, i + 1) for i in range(9)], ws)
+    _, st = oracle.govm(rp, cl, w, 0)
+    assert (st["steps"], st["edges_scanned"], st["updates"], st["converged"]) == (10, 9, 9, 1)
+    _, st = oracle.gsvm(rp, cl, w, 0)
+    assert (st["steps"], st["edges_scanned"], st["updates"], st["converged"]) == (2, 18, 9, 1)
+
+
+@pytest.mark.parametrize("alg", ("govm", "gsvm"))
+@pytest.mark.parametrize("kind", ("u32", "f32"))
+def test_iterations_stop_when_a_step_changes_nothing(alg, kind):
+    # both algorithms end by their "no path changed" test, long before the
+    # step cap n; a step that changes nothing scans every edge it would scan
+    # again, so a run that never stops would hit the cap
+    rp, cl, w = gg.random_small(300, 2400, 5, kind=kind, wlo=1, whi=20)
+    _, st = oracle.govm(rp, cl, w, 0, algorithm=alg)
+    assert st["converged"] == 1 and st["steps"] < 300 // 2
+
+
 @pytest.mark.parametrize("alg", ALL)
 def test_complete_graph_squared_weights(alg):
     # edges i -> j (i < j) with weight (j - i)^2: unit steps win, dist[j] = j.
@@ -575,3 +600,52 @@ def test_bellman_ford_path_against_csr_order_needs_n_minus_1_rounds():
     assert not neg and d_bf.tolist() == expect
     d, st = oracle.govm(rp, cl, w, n - 1)
     assert d.tolist() == expect and st["steps"] == n
+
+
+def test_signed_certificate_rejects_planted_mistakes():
+    # int32 weights with negative edges (potential reweighting, no negative
+    # cycle): the certificate accepts the oracle's result and rejects a
+    # non-tight parent edge (code 3) and a consistent tree that misses a
+    # shorter edge (code 2)
+    rp, cl, w, w2, p = potential_reweighted(120, 800, 3)
+    d, neg = oracle.bellman_ford(rp, cl, w2, 0)
+    assert not neg
+    pe = oracle.parent_edges(rp, cl, w2, 0, d)
+    assert oracle.certificate(rp, cl, w2, 0, d, pe) == (0, -1)
+    tails = oracle.edge_tails(rp)
+    fin = d != oracle.I32_INF
+    # a reached vertex with an in-edge that is not tight
+    cand = [e for e in range(len(cl)) if pe[cl[e]] >= 0 and e != pe[cl[e]] and fin[tails[e]]
+            and int(d[tails[e]]) + int(w2[e]) != int(d[cl[e]])]
+    assert cand
+    bad = pe.copy()
+    bad[cl[cand[0]]] = cand[0]
+    assert oracle.certificate(rp, cl, w2, 0, d, bad) == (3, int(cl[cand[0]]))
+    # drop a tree edge whose removal lengthens some path
+    for e_star in sorted(int(e) for e in pe[pe >= 0]):
+        keep = np.ones(len(cl), bool)
+        keep[e_star] = False
+        rp2, cl2, w22 = gg.csr_from_edges(len(rp) - 1, np.stack([tails[keep], cl[keep]], 1), w2[keep], np.int32)
+        d2, neg2 = oracle.bellman_ford(rp2, cl2, w22, 0)
+        if neg2 or np.array_equal(d2, d):
+            continue
+        pe2 = oracle.parent_edges(rp2, cl2, w22, 0, d2)
+        full = np.nonzero(keep)[0]
+        pe2_full = np.where(pe2 >= 0, full[np.maximum(pe2, 0)], -1).astype(np.int32)
+        assert oracle.certificate(rp2, cl2, w22, 0, d2, pe2) == (0, -1)
+        assert oracle.certificate(rp, cl, w2, 0, d2, pe2_full)[0] == 2
+        return
+    pytest.fail("no tree edge whose removal lengthens a path")
+
+
+def test_signed_distance_outside_int32_is_reported():
+    # path sums of -2^30 three times reach -3 * 2^30 < -2^31: the oracle works
+    # in int64 and refuses to hand back a value that int32 cannot hold
+    rp, cl, w = gg.csr_from_edges(4, [(0, 1), (1, 2), (2, 3)], np.full(3, -(1 << 30), np.int32), np.int32)
+    with pytest.raises(OverflowError):
+        oracle.bellman_ford(rp, cl, w, 0)
+    with pytest.raises(OverflowError):
+        oracle.govm(rp, cl, w, 0)
+    # two steps still fit: -2^31 is the smallest int32
+    rp, cl, w = gg.csr_from_edges(3, [(0, 1), (1, 2)], np.full(2, -(1 << 30), np.int32), np.int32)
+    assert oracle.bellman_ford(rp, cl, w, 0)[0].tolist() == [0, -(1 << 30), -(1 << 31)]

@@ -143,7 +143,33 @@ MUTANTS = [
     ("bellman_ford_i32: one round short", C,
      "  for (int32_t round = 0; round < n - 1; ++round) {", "  for (int32_t round = 0; round < n - 2; ++round) {",
      None),
+    ("gsvm_u32: relaxation test loosened to >=", C,
+     "            if (alpha[index] > alpha[j] + value && !is_root[index]) {\n              alpha[index] = alpha[j] + value;\n"
+     "              count[index]++;",
+     "            if (alpha[index] >= alpha[j] + value && !is_root[index]) {\n              alpha[index] = alpha[j] + value;\n"
+     "              count[index]++;", None),
+    ("govm_i32: relaxation test loosened to >=", C,
+     "          int64_t value = w[e];\n          st->edges_scanned++;\n          if (alpha[index] > alpha[j] + value && !is_root[index]) {",
+     "          int64_t value = w[e];\n          st->edges_scanned++;\n          if (alpha[index] >= alpha[j] + value && !is_root[index]) {",
+     None),
+    ("parents_i32: last matching edge wins", C,
+     "      if (is_root[v] || parent_edge[v] != -1) continue;\n      if (dist[u] + w[e] == dist[v]) parent_edge[v] = e;",
+     "      if (is_root[v]) continue;\n      if (dist[u] + w[e] == dist[v]) parent_edge[v] = e;", 1),
+    ("cert_i32: edge-relaxation check dropped", C,
+     "      if (!is_root[col[e]] && dist[u] + w[e] < dist[col[e]]) { rc = 2; *where = e; break; }",
+     "      if (0) { rc = 2; *where = e; break; }", 1),
+    ("cert_i32: parent edge tightness not checked", C,
+     "    if (!finite[lo] || dist[lo] + w[e] != dist[v]) { rc = 3; *where = v; }",
+     "    if (!finite[lo]) { rc = 3; *where = v; }", 1),
     # Pure Python / numpy routines of the oracle
+    ("_u64_to_u32: distances past the sentinel silently truncated", PY,
+     "    if np.any(d[fin] >= np.uint64(0xFFFFFFFF)):\n        raise OverflowError(\"a shortest distance does not fit below 0xFFFFFFFF\")",
+     "    if False:\n        raise OverflowError(\"a shortest distance does not fit below 0xFFFFFFFF\")", None),
+    ("_i64_to_i32: negative overflow not checked", PY,
+     " or np.any(d[fin] < np.int64(-2 ** 31)):", ":", None),
+    ("edge_tails: tails shifted by one row", PY,
+     "    return np.repeat(np.arange(len(row_ptr) - 1, dtype=np.int32), np.diff(row_ptr))",
+     "    return np.repeat(np.arange(1, len(row_ptr), dtype=np.int32) % (len(row_ptr) - 1), np.diff(row_ptr))", None),
     ("dense_colmin: transposed operand in A_s[k, j] = a_s[k] + a[k, j]", PY,
      "        As = a[:, None] + A", "        As = a[None, :] + A", None),
     ("brute_force: path value folded in double, not fp32", PY,
