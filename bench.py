@@ -844,7 +844,7 @@ def main_ours(args):
         raise SystemExit(f"unknown workload {args.workload}")
 
 
-def main():
+def build_parser() -> argparse.ArgumentParser:
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
@@ -856,7 +856,11 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch shape (no autotuning)")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--sources", type=int, default=0, help="limit sources per step (profiling runs)")
-    args = ap.parse_args()
+    return ap
+
+
+def main():
+    args = build_parser().parse_args()
     if args.warmup < 3:
         log("[bench] warm-up raised to 3 steps")
         args.warmup = 3

@@ -4,6 +4,7 @@ traffic by kernel-source hash, and the oracle legs that sit beside the GPU
 results."""
 import json
 import os
+import re
 import subprocess
 import sys
 
@@ -70,3 +71,39 @@ def test_oracle_legs_beside_batched_and_backward_results():
     c[wd.extra["targets"]] = wd.extra["coef"]
     g = oracle.subtree_grad(wd.row_ptr, wd.col, wd.weights, 0, c).astype(np.float32)
     assert bench.cpu_leg_diff(wd, c, g)["max_abs_err_over_max_ref"] < 1e-6
+
+
+def _bench_commands(text):
+    """Argument lists of every `python bench.py ...` command quoted in a
+    profile summary (continuation lines joined, redirections and pipes cut)."""
+    import shlex
+    joined = text.replace("\\\n", " ")
+    out = []
+    for line in joined.splitlines():
+        i = line.find("python bench.py")
+        if i < 0:
+            continue
+        rest = line[i + len("python bench.py"):]
+        for stop in ("&&", ">", "|", "#", "`"):
+            rest = rest.split(stop)[0]
+        out.append(shlex.split(rest))
+    return out
+
+
+def test_profile_commands_run_committed_files_with_current_flags():
+    known = {"grid", "tiny", "batched", "diff", "mu", "apsp", "gsvm"}
+    pdir = os.path.join(ROOT, "profiles")
+    files = sorted(f for f in os.listdir(pdir) if f.endswith(".md"))
+    assert files
+    for f in files:
+        with open(os.path.join(pdir, f)) as fh:
+            text = fh.read()
+        cmds = _bench_commands(text)
+        assert cmds, f"{f} quotes no bench.py command"
+        for argv in cmds:
+            args = bench.build_parser().parse_args(argv)
+            w = args.workload
+            assert w in known or (w.startswith("rmat") and w[4:].isdigit()), (f, w)
+        ncu_lines = [l for l in text.replace("\\\n", " ").splitlines() if re.search(r"(^|&&)\s*ncu\s", l.strip())]
+        for line in ncu_lines:
+            assert "--clock-control none" in line, (f, line)
