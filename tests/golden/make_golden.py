@@ -38,6 +38,9 @@ def write(name, wl, source):
         "parent": [int(x) for x in parent],
         "parent_edge": [int(x) for x in pe],
         "written_by": "tests/golden/make_golden.py (oracle.sssp: binary-heap Dijkstra + lowest-index parent rule)",
+        "follows": "distances: the fixpoint of Algorithm 2 (Section 3.4), equal to the shortest-path distances of "
+                   "Section 2.1 (fp32 weights as left-folded round-to-nearest sums, Section 4.2); parents: the "
+                   "library's lowest-index tight-edge rule (the paper returns distances only)",
     }
     with open(os.path.join(HERE, name), "w") as f:
         json.dump(rec, f)
