@@ -8,8 +8,8 @@
  * frontier delta) are expanded; vertices whose distance changes in this step
  * form the next frontier (beta); the iteration stops when a step changes
  * nothing.  This yields single-source shortest paths (SSSP), and multi-source
- * / all-pairs shortest paths as repeated SSSP (Section 3.4, "time complexity
- * of DAWN for APSP tasks"; Section 1, contribution 5 on MSSP).
+ * / all-pairs shortest paths as repeated SSSP (Section 3.4, the complexity
+ * argument for APSP; Section 1, contribution 5 on MSSP).
  *
  * Conventions shared by every entry point
  * ---------------------------------------
@@ -32,7 +32,7 @@
  *    Section 1 contribution 4) report int32 distances with 0x7FFFFFFF
  *    (INT32_MAX) for unreachable vertices.
  *  - Negative weights (int32 graphs): the iteration is capped at n steps as
- *    in Algorithm 2 ("while step < n"); without a negative cycle reachable
+ *    in Algorithm 2 (its loop runs at most n steps); without a negative cycle reachable
  *    from a source it converges before the cap, with one the solve reports
  *    DAWN_ERR_NOT_CONVERGED and its outputs are the state after n steps.
  *  - Parents: parent[v] is the tail u of the lowest-index CSR edge e = (u->v)
@@ -106,7 +106,9 @@ int dawn_create_graph(int32_t n, int64_t m, const int32_t *row_ptr, const int32_
 
 /*
  * Replace the edge weights (same type and count as at creation), e.g. after
- * a gradient step.  Same validation and ownership rules as creation.
+ * a gradient step.  These are the values array of A_CSR (Section 3.2); the
+ * paper has no weight update, this is a library addition for training
+ * loops.  Same validation and ownership rules as creation.
  *   flags  DAWN_WEIGHTS_ON_DEVICE: `weights` is device memory (else host);
  *          DAWN_WEIGHTS_DEFER_CHECK: do not wait for the validation result.
  *          The call then returns DAWN_OK without synchronising, and a later
@@ -121,6 +123,7 @@ enum { DAWN_WEIGHTS_ON_DEVICE = 1, DAWN_WEIGHTS_DEFER_CHECK = 2 };
 int dawn_set_weights(dawn_graph g, const void *weights, int flags, void *stream);
 
 /*
+ * Library plumbing with no counterpart in the paper.
  * Pre-size the solver workspace for batches of up to k instances (optional;
  * solves grow it on demand).  Call before capturing solves into a CUDA
  * graph, since growing the workspace allocates device memory.  (Solves by
@@ -146,8 +149,8 @@ int dawn_sssp(dawn_graph g, int32_t source, void *dist, int32_t *parent, int32_t
 /*
  * Multi-source shortest paths: k independent SSSP instances, one per source,
  * relaxed together with per-instance frontiers (Section 1, contribution 5;
- * the paper's "each thread accesses paths from different starting points",
- * Section 3.5).  APSP is the case sources = 0..n-1.
+ * Section 3.5, where the paper parallelises across starting vertices).  APSP
+ * is the case sources = 0..n-1.
  *   sources      device int32[k]; an entry outside [0, n) makes the solve
  *                fail with DAWN_ERR_INVALID in dawn_status()
  *   k            number of instances, k >= 1
@@ -162,7 +165,8 @@ int dawn_msssp(dawn_graph g, const int32_t *sources, int32_t k, void *dist, int3
 
 /*
  * One shortest-path forest grown from several roots at distance 0 (all roots
- * are "sources" for the index != source guard of Algorithm 2).  On a graph
+ * are sources for Algorithm 2's source guard, which never relaxes an edge
+ * into a source).  On a graph
  * that is the disjoint union of many graphs with one root each, this solves
  * every graph in one launch.
  *   roots        device int32[k] (duplicates allowed), k >= 1
@@ -173,6 +177,8 @@ int dawn_sssp_roots(dawn_graph g, const int32_t *roots, int32_t k, void *dist, i
 
 /*
  * Backward pass of dist with respect to the edge weights (float32 graphs).
+ * The paper has no backward pass; this is a library addition that follows
+ * from the forward result: the parent tree the GOVM fixpoint defines.
  * dist[v] is the sum of the weights along v's tree path, so for a loss L,
  * dL/dw[e] = sum of dL/ddist[t] over the subtree below tree edge e, and 0 for
  * edges off the tree.  The parent tree from the forward solve is the only
@@ -194,6 +200,7 @@ int dawn_sssp_backward(dawn_graph g, const int32_t *parent_edge, const float *gr
                        void *stream);
 
 /*
+ * Library plumbing with no counterpart in the paper.
  * Device-side status of the last solve on this handle (DAWN_OK or an error
  * code).  With sync != 0 the call first waits for the last stream used by the
  * handle; with sync == 0 it reads the status without waiting (it may be
@@ -201,12 +208,14 @@ int dawn_sssp_backward(dawn_graph g, const int32_t *parent_edge, const float *gr
  */
 int dawn_status(dawn_graph g, int sync);
 
-/* Counters of the last solve (waits for it). */
+/* Counters of the last solve (waits for it): steps of Algorithm 2's loop,
+ * frontier sizes, edges scanned (the work of Section 3.4's complexity
+ * argument) and path updates (mu's numerator, Section 4.2). */
 int dawn_get_stats(dawn_graph g, dawn_stats *out);
 
 /*
  * Tuning and test options.
- *   DAWN_OPT_MAX_STEPS     step cap (default n, as in "while step < n")
+ *   DAWN_OPT_MAX_STEPS     step cap (default n, the step bound of Algorithm 2)
  *   DAWN_OPT_WAIT_LIMIT_NS bound on every in-kernel wait (default 4e9 ns)
  *   DAWN_OPT_GRID_BLOCKS   persistent grid size (0 = automatic: all
  *                          co-resident CTAs for large problems, fewer for
@@ -310,7 +319,8 @@ int dawn_autotune(dawn_graph g, int mode, const int32_t *sources, int32_t k, int
  */
 int dawn_get_trace(dawn_graph g, int64_t *out, int32_t cap);
 
-/* Basic graph facts: n, m and the weight type. */
+/* Basic graph facts: n, m and the weight type (plumbing; no counterpart in
+ * the paper). */
 int dawn_graph_info(dawn_graph g, int32_t *n, int64_t *m, int *wtype);
 
 /*
@@ -341,10 +351,10 @@ int dawn_graph_info(dawn_graph g, int32_t *n, int64_t *m, int *wtype);
 int dawn_sssp_noalloc(dawn_graph g, int32_t source, void *dist, int32_t *parent, int32_t *parent_edge,
                       int32_t *status_out, void *stream);
 
-/* Human-readable name of a status code (static string). */
+/* Human-readable name of a status code (static string; plumbing). */
 const char *dawn_status_string(int code);
 
-/* Free the graph and its device memory.  NULL is allowed. */
+/* Free the graph and its device memory.  NULL is allowed (plumbing). */
 void dawn_destroy(dawn_graph g);
 
 #ifdef __cplusplus

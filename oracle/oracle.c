@@ -25,12 +25,14 @@
  * Readings of the paper taken here (all are listed in the design notes):
  *   - alpha starts at +inf except alpha[source] = 0, delta = {source},
  *     beta = {}, step = 0 (the paper does not state the initialisation);
- *   - "If alpha[j]" in Algorithm 1 means "alpha[j] is finite" (reached);
+ *   - Algorithm 1 tests alpha[j] as a truth value; read here as alpha[j]
+ *     being finite (the vertex is reached);
  *   - after each GOVM step delta takes beta's contents and beta is cleared
  *     (the listing copies beta into delta without clearing beta);
- *   - several roots may be given; all start at 0 and the "index != source"
- *     guard skips every root (single-source SSSP is the case k = 1);
- *   - the loop is capped at n steps as in both algorithms (while step < n);
+ *   - several roots may be given; all start at 0 and the source guard (no
+ *     edge is relaxed into a source) covers every root; single-source SSSP
+ *     is the case k = 1;
+ *   - the loop is capped at n steps, the bound both algorithms state;
  *     a run that reaches the cap reports "not converged".
  *
  * Parity unpinned: the work counters of govm_* / gsvm_* (steps, edges

@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(kSmallThreads) govm_small_kernel(GovmParams p,
         const uint32_t ckey = Key<WT>::add(du, c.y);
         const unsigned long long cand = ((unsigned long long)ckey << 32) | (uint32_t)x;
         const unsigned long long cur = st[t];
-        if (cand < cur && cur != kSourceState) {  // the `index != source` guard
+        if (cand < cur && cur != kSourceState) {  // the source guard: never relax into a source
           const unsigned long long old = atomicMin(st + t, cand);
           if (ckey < (uint32_t)(old >> 32)) atomicOr(bm + (t >> 5), 1u << (t & 31));
         }

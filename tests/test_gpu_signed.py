@@ -78,7 +78,7 @@ def test_signed_overflow_bound_rejected(dawn):
     w = np.array([-(1 << 29), 5], np.int32)
     g = dawn.Graph(rp, np.array([1, 0], np.int32), w)
     # 0 -> 1 -> 0 has negative length, but it runs through the source, and
-    # Algorithm 2's "index != source" guard never relaxes into a source: the
+    # Algorithm 2's source guard never relaxes into a source: the
     # solve converges (the oracle agrees)
     d, _, _ = g.sssp(0)
     assert d.cpu().tolist() == [0, -(1 << 29)]

@@ -135,7 +135,7 @@ def test_single_vertex_and_no_edges(alg):
 
 @pytest.mark.parametrize("alg", ALL)
 def test_edges_into_source_ignored(alg):
-    # the "index != source" guard: a zero-weight edge back into the source
+    # the source guard: a zero-weight edge back into the source
     rp, cl, w = gg.csr_from_edges(3, [(0, 1), (1, 0), (1, 2)], [0, 0, 5])
     d = run(alg, rp, cl, w, 0)
     assert d.tolist() == [0, 0, 5]
@@ -579,7 +579,7 @@ def test_negative_cycle_reported():
 
 def test_negative_cycle_through_the_source_is_excluded_by_the_guard():
     # 0->1 (1), 1->0 (-5), 1->2 (2): the cycle 0->1->0 has length -4 but only
-    # re-enters the source, whose distance the "index != source" guard keeps
+    # re-enters the source, whose distance the source guard keeps
     # at 0 (Algorithm 2); so dist = [0, 1, 3] and the run converges.
     rp, cl, w = gg.csr_from_edges(3, [(0, 1), (1, 0), (1, 2)], np.array([1, -5, 2], np.int32), np.int32)
     d, st = oracle.govm(rp, cl, w, 0)
