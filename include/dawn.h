@@ -330,17 +330,28 @@ int dawn_graph_info(dawn_graph g, int32_t *n, int64_t *m, int *wtype);
  * For callers that cannot allocate device memory during a call (a memory
  * budget fixed up front, hosts that forbid allocator calls after start-up,
  * or code that must avoid the implicit synchronisation of cudaMalloc /
- * cudaFree), this entry point runs the same GOVM solve as dawn_sssp but takes
- * its whole per-solve workspace from one fixed array of 32 MiB in device
- * global memory that belongs to the library (every GPU that loads the
- * library holds this array until the process exits).  It calls no
- * allocation routine.
+ * cudaFree), this entry point runs the persistent GOVM kernel of dawn_sssp
+ * (Algorithm 2, or Algorithm 1 under DAWN_OPT_GSVM) but takes its whole
+ * per-solve workspace from one fixed array of 32 MiB in device global memory
+ * that belongs to the library (every GPU that loads the library holds this
+ * array until the process exits).  It calls no allocation routine.
  *   g            a graph created earlier with dawn_create_graph
  *   source, dist, parent, parent_edge   as for dawn_sssp
  *   status_out   device int32 or NULL: receives the solve's device-side
  *                status (DAWN_OK or an error code) when the solve ends
- * Limit: the workspace needs about 24 bytes per vertex plus 4 bytes per 128
- * edges; a graph that does not fit in 32 MiB is rejected with
+ * The solve's status and counters are also copied into the handle, so
+ * dawn_status(g, 1), dawn_get_stats and dawn_get_trace report this call like
+ * any other solve, and dawn_destroy waits for its stream.
+ * Options: DAWN_OPT_MAX_STEPS, DAWN_OPT_WAIT_LIMIT_NS, DAWN_OPT_GRID_BLOCKS,
+ * DAWN_OPT_CTAS_PER_SM, DAWN_OPT_GSVM, DAWN_OPT_TRACE_STEPS (the trace
+ * buffer is allocated when the option is set) and DAWN_OPT_TEST_STALL apply
+ * as for dawn_sssp.  DAWN_OPT_SMALL_PATH does not: the small-graph kernel is
+ * never used, so the results are the same but the time may differ.
+ * Limit: the workspace takes R(64) + R(16) + R(8 n) + R(4 ceil(n / 32)) +
+ * R(16 n) + R(4 (floor(m / 128) + 2)) bytes, where R(x) rounds x up to a
+ * multiple of 256 (about 24.125 bytes per vertex plus 4 bytes per 128 edges
+ * plus at most 1.5 KB; with m = 16 n, up to about 1.35 M vertices); a graph
+ * whose workspace exceeds 32 MiB (33,554,432 bytes) is rejected with
  * DAWN_ERR_INVALID before anything is enqueued.
  * The first call on a device looks up the array's device address (once per
  * device); make that first call before any stream capture.  Every call uses

@@ -787,17 +787,25 @@ extern "C" int dawn_sssp_noalloc(dawn_graph g, int32_t source, void *dist, int32
   p.ctl = ctl;
   p.max_steps = g->max_steps > 0 ? g->max_steps : g->n;
   p.wait_limit_ns = g->wait_limit_ns;
-  p.test_stall = 0;
-  p.trace = nullptr;
-  p.trace_cap = 0;
+  p.test_stall = g->test_stall;
+  p.gsvm = g->gsvm;
+  p.trace = g->trace;  // allocated when the option was set, not here
+  p.trace_cap = g->trace_cap;
   p.vflags = g->vflags;
   p.vlimit = weight_limit(g->wtype);
   // the control block (barrier counters, status) must start at zero; the
   // kernel itself resets everything else it reads
   cudaError_t e = cudaMemsetAsync(ctl, 0, sizeof(DeviceCtl), s);
+  if (e == cudaSuccess && g->trace)
+    e = cudaMemsetAsync(g->trace, 0, (size_t)g->trace_cap * 4 * sizeof(unsigned long long), s);
   if (e == cudaSuccess) e = dawn::launch_govm(p, g->wtype, kernel_ctas(g), grid_for(g, 1), s);
+  // the handle's own control block receives this solve's status and
+  // counters, so dawn_status / dawn_get_stats report it like any other solve
+  if (e == cudaSuccess) e = cudaMemcpyAsync(g->ctl, ctl, sizeof(DeviceCtl), cudaMemcpyDeviceToDevice, s);
   if (e == cudaSuccess && status_out)
     e = cudaMemcpyAsync(status_out, &ctl->status, sizeof(int32_t), cudaMemcpyDeviceToDevice, s);
   if (e != cudaSuccess) return cuda_fail(e);
+  g->last_k = 1;
+  g->last_stream = s;  // dawn_status(g, 1), dawn_get_stats and dawn_destroy wait on it
   return DAWN_OK;
 }
