@@ -11,13 +11,22 @@ roofline of the persistent kernel (algorithmic bytes from the solver's own
 counters / CUDA-event launch time, against the measured HBM copy bandwidth),
 the end-to-end GTEPS through the C ABI from pinned host buffers (graph copy
 in, solves, dist + parent copied out), the CPU oracle on a bounded sample, and
-the SM clocks sampled during the timed region.
+the SM clocks sampled during the timed region.  At N = 1 the same line also
+carries the rest of the metric, each leg with its own clocks, roofline, L2
+rule and oracle leg: grid_2048_f32 (the high-diameter grid, 16 sources),
+msssp_rmat18_1024 and roots_er64 (batched forms vs a loop of the plain
+solver) and diff_rmat16_f32 (forward + backward vs the plain solver), plus
+the random-gather rate of the GPU (gather_ceiling).  --no-legs skips them.
 
 Other workloads (--workload): grid (2048^2 fp32 grid with shortcuts, 16
 sources), batched (R-MAT s18 with 1024 sources in msssp launches vs a loop
 of single solves; 64 uneven ER graphs in one multi-root launch vs a loop),
 diff (R-MAT s16 fp32: forward, forward+backward, plain solve), tiny
-(ER n=1024).
+(ER n=1024), apsp, mu, gsvm.
+
+L2 rule: a workload whose graph (row_ptr and the column/weight pairs) is
+larger than L2 is timed back to back; a smaller one gets L2 flushed before
+every timed call, outside the call's CUDA events.
 
 --impl reference times the CPU oracle (the literal GOVM iteration) on the
 host cores instead; under torchrun only rank 0 runs it.
@@ -95,50 +104,152 @@ def dist_env():
 
 
 class Clocks:
-    """nvidia-smi sampling of SM clocks and throttle reasons (200 ms)."""
+    """nvidia-smi sampling of SM clocks, utilisation and throttle reasons
+    every 200 ms.  Entering waits (up to 2 s) for the first sample, so the
+    samples cover the region that follows; the summary's sm_mhz is the median
+    over samples taken under load (utilisation > 0) when there are any."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-         "clocks_event_reasons.sw_power_cap")
+         "clocks_event_reasons.sw_power_cap,utilization.gpu")
 
     def __init__(self, index: int):
         self.index = index
         self.p = None
+        self.lines = []
+
+    def _read(self):
+        for line in self.p.stdout:
+            if line.strip():
+                self.lines.append(line)
+                self._first.set()
 
     def __enter__(self):
+        import threading
+        self.lines = []
+        self._first = threading.Event()
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
                                        "-lms", "200", "-i", str(self.index)], stdout=subprocess.PIPE,
                                       stderr=subprocess.DEVNULL, text=True)
         except OSError:
             self.p = None
+            return self
+        self._t = threading.Thread(target=self._read, daemon=True)
+        self._t.start()
+        self._first.wait(2.0)
         return self
 
     def __exit__(self, *exc):
-        self.lines = []
         if self.p is not None:
             time.sleep(0.25)
             self.p.terminate()
-            out, _ = self.p.communicate(timeout=10)
-            self.lines = [l for l in out.splitlines() if l.strip()]
+            try:
+                self.p.wait(timeout=10)
+            except subprocess.TimeoutExpired:
+                self.p.kill()
+            self._t.join(timeout=10)
 
     def summary(self):
-        sm, smax, reasons = [], None, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for l in getattr(self, "lines", []):
-            f = [x.strip() for x in l.split(",")]
-            if len(f) < 9:
-                continue
-            try:
-                sm.append(float(f[1]))
-                smax = float(f[2])
-            except ValueError:
-                continue
-            for nm, v in zip(names, f[5:9]):
-                if v.lower() == "active":
-                    reasons.add(nm)
-        if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
-        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+        return clocks_summary(self.lines)
+
+
+def clocks_summary(lines):
+    """Median SM clock under load, the maximum clock and every throttle
+    reason seen, from nvidia-smi CSV lines (fields as in Clocks.Q)."""
+    sm, busy, smax, reasons = [], [], None, set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for l in lines:
+        f = [x.strip() for x in l.split(",")]
+        if len(f) < 9:
+            continue
+        try:
+            sm.append(float(f[1]))
+            smax = float(f[2])
+        except ValueError:
+            continue
+        try:
+            if len(f) > 9 and float(f[9]) > 0:
+                busy.append(sm[-1])
+        except ValueError:
+            pass
+        for nm, v in zip(names, f[5:9]):
+            if v.lower() == "active":
+                reasons.add(nm)
+    if not sm:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+    use = busy or sm
+    return {"sm_mhz": float(np.median(use)), "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm),
+            "samples_under_load": len(busy)}
+
+
+# ------------------------------------------------------------------ L2 rule
+
+L2_FALLBACK = 132 * 1024 * 1024  # GB300: 129 MB (in MiB units as the device reports)
+
+
+def l2_bytes(device=0) -> int:
+    import torch
+    try:
+        return int(getattr(torch.cuda.get_device_properties(device), "L2_cache_size", 0)) or L2_FALLBACK
+    except Exception:
+        return L2_FALLBACK
+
+
+def graph_bytes(n: int, m: int) -> int:
+    """Device bytes of the arrays a solve streams: row_ptr (4 (n+1)) and the
+    interleaved (column, weight) pairs (8 m)."""
+    return 4 * (n + 1) + 8 * m
+
+
+def l2_rule(n: int, m: int, l2: int):
+    """(flush, note): flush L2 before every timed call when the graph could
+    stay L2-resident between calls, and the sentence that says which."""
+    gb = graph_bytes(n, m)
+    if gb > l2:
+        return False, (f"graph larger than L2 (row_ptr + column/weight pairs {gb / 1e6:.0f} MB > L2 "
+                       f"{l2 / 1e6:.0f} MB); no flush between timed calls")
+    return True, (f"graph fits in L2 (row_ptr + column/weight pairs {gb / 1e6:.1f} MB <= L2 {l2 / 1e6:.0f} MB); "
+                  f"L2 flushed (a {2 * l2 / 1e6:.0f} MB write) before every timed call, outside its CUDA events")
+
+
+class L2Flush:
+    """Writes a buffer twice the size of L2, evicting whatever a previous
+    call left there."""
+
+    def __init__(self, device=0):
+        import torch
+        self.buf = torch.empty(2 * l2_bytes(device) // 4, dtype=torch.int32, device=device)
+        self.k = 0
+
+    def __call__(self):
+        self.k += 1
+        self.buf.fill_(self.k)
+
+
+def timed_calls(fn, reps: int, flush=None, warm: int = 1):
+    """CUDA-event seconds of each of `reps` calls of fn on the current
+    stream, after `warm` untimed calls; with `flush`, L2 is flushed before
+    every call, outside the events."""
+    import torch
+    stream = torch.cuda.current_stream()
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for a, b in evs:
+        if flush is not None:
+            flush()
+        a.record(stream)
+        fn()
+        b.record(stream)
+    torch.cuda.synchronize()
+    return np.array([a.elapsed_time(b) for a, b in evs]) / 1e3
+
+
+def reps_for(fn, seconds: float, lo: int = 3, hi: int = 4000) -> int:
+    """Calls of fn that fill about `seconds` of device time (one probe)."""
+    t = timed_calls(fn, 1, warm=1)[0]
+    return int(max(lo, min(hi, seconds / max(t, 1e-6))))
 
 
 # ------------------------------------------------------------------ workloads
@@ -189,14 +300,19 @@ def host_threads(units: int) -> int:
 
 # --------------------------------------------------------------- our solver
 
-def run_sssp_bench(args, wl, device, world, rank):
+def run_sssp_bench(args, wl, device, world, rank, steps=None, keep_dist=True):
+    """Device-timed single-source solves: `steps` (default --steps) timed
+    steps of one dawn_sssp per source, after --warmup untimed steps."""
     import torch
     import paper_2306_07872_gb300 as dawn
 
     torch.cuda.set_device(device)
     stream = torch.cuda.current_stream()
+    steps = args.steps if steps is None else steps
     g = dawn.Graph(wl.row_ptr, wl.col, wl.weights, device=device)
     S = len(wl.sources)
+    flush_needed, l2note = l2_rule(wl.n, wl.m, l2_bytes(device))
+    flush = L2Flush(device) if flush_needed else None
     tuning = None
     if not args.no_tune:  # launch shape picked by the library's autotuner (untimed setup, like the upload)
         t = time.perf_counter()
@@ -227,21 +343,26 @@ def run_sssp_bench(args, wl, device, world, rank):
         stats.append(dawn.dawn_get_stats(g.handle))
     # timed region
     evs = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in srcs]
-           for _ in range(args.steps)]
+           for _ in range(steps)]
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     barrier(world)
     torch.cuda.synchronize()
     with Clocks(device) as clk:
         t0.record(stream)
-        for k in range(args.steps):
+        for k in range(steps):
+            if flush is not None:  # between timed steps, outside their events
+                flush()
             step(evs[k])
         t1.record(stream)
         torch.cuda.synchronize()
     barrier(world)
     g.check()
-    dist_host = dist.cpu().numpy() if (rank == 0 and not args.no_cpu) else None
-    elapsed = t0.elapsed_time(t1) / 1e3
+    dist_host = dist.cpu().numpy() if (rank == 0 and not args.no_cpu and keep_dist) else None
+    if flush is None:
+        elapsed = t0.elapsed_time(t1) / 1e3
+    else:  # each step from its first launch's start to its last launch's end
+        elapsed = sum(row[0][0].elapsed_time(row[-1][1]) for row in evs) / 1e3
     elapsed = max_over_ranks(elapsed, world)
     launch_ms = np.array([[a.elapsed_time(b) for a, b in row] for row in evs])  # [K, S]
     per_src_ms = launch_ms.mean(axis=0)
@@ -265,7 +386,10 @@ def run_sssp_bench(args, wl, device, world, rank):
         "dist_host": dist_host,
         "tuning": tuning,
         "elapsed": elapsed,
-        "gteps": S * args.steps * world * wl.e_wcc / elapsed / 1e9,
+        "gteps": S * steps * world * wl.e_wcc / elapsed / 1e9,
+        "steps": steps,
+        "l2": l2note,
+        "flushed": flush is not None,
         "launch_ms_mean": float(launch_ms.mean()),
         "launch_ms_median": float(np.median(launch_ms)),
         "gteps_median": float(np.median(wl.e_wcc / (per_src_ms / 1e3) / 1e9)),
@@ -280,7 +404,8 @@ def run_sssp_bench(args, wl, device, world, rank):
         "edges_scanned_mean": float(np.mean([st["edges_scanned"] for st in stats])),
         "steps_mean": float(np.mean([st["steps"] for st in stats])),
         "clocks": clk.summary(),
-        "launches": S * args.steps,
+        "launches": S * steps,
+        "frontier_sum_mean": float(np.mean([st["frontier_sum"] for st in stats])),
         "stats0": stats[0],
     }
     g.close()
@@ -365,29 +490,35 @@ def run_e2e(args, wl, device, world, tuning=None):
             "d2h_bytes_per_step": int(d2h), "steps": steps, "ms_per_step": el / steps * 1e3}
 
 
-def cpu_baseline(wl, budget_s: float = 20.0, gpu_dist=None):
+def cpu_baseline(wl, budget_s: float = 20.0, gpu_dist=None, single_core: bool = True):
     """The oracle's literal GOVM iteration (Algorithm 2) on the host cores,
     one source per thread, on a bounded sample of the sources; plus the
     single-core time of one source by Algorithm 2 and by Dijkstra.  With
     `gpu_dist` (row i = the GPU's distances from source i) every sampled
-    source is also compared bit for bit with the GPU."""
+    source is also compared bit for bit with the GPU.  single_core=False
+    (workloads whose one-source solve takes many seconds) skips the
+    single-core probes and runs one round of one source per thread."""
     import oracle
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
     threads = max(1, min(cores, 16, len(wl.sources)))
-    # one probe solve sizes the sample to the time budget
-    t, _ = oracle.timed_govm(wl.row_ptr, wl.col, wl.weights, [int(wl.sources[0])], threads=1)
-    t0 = time.perf_counter()
-    oracle.dijkstra(wl.row_ptr, wl.col, wl.weights, int(wl.sources[0]))
-    t_dij = time.perf_counter() - t0
-    rounds = max(1, int(budget_s / max(t, 1e-3) / 2))
+    if single_core:
+        # one probe solve sizes the sample to the time budget
+        t, _ = oracle.timed_govm(wl.row_ptr, wl.col, wl.weights, [int(wl.sources[0])], threads=1)
+        t0 = time.perf_counter()
+        oracle.dijkstra(wl.row_ptr, wl.col, wl.weights, int(wl.sources[0]))
+        t_dij = time.perf_counter() - t0
+        rounds = max(1, int(budget_s / max(t, 1e-3) / 2))
+    else:
+        rounds = 1
     nsrc = min(len(wl.sources), threads * rounds)
     sample = [int(s) for s in wl.sources[:nsrc]]
     el, res = oracle.timed_govm(wl.row_ptr, wl.col, wl.weights, sample, threads=threads)
     out = {"value": len(sample) * wl.e_wcc / el / 1e9, "unit": "GTEPS", "cores": threads, "kind": "oracle",
            "sample": f"{len(sample)} of the {len(wl.sources)} sources, literal GOVM (Algorithm 2), "
                      f"one source per thread, {threads} threads, {el:.1f} s",
-           "mu_oracle": float(np.mean([r[1]["mu"] for r in res])),
-           "single_core_ms_per_source": {"govm_alg2": t * 1e3, "dijkstra": t_dij * 1e3}}
+           "mu_oracle": float(np.mean([r[1]["mu"] for r in res]))}
+    if single_core:
+        out["single_core_ms_per_source"] = {"govm_alg2": t * 1e3, "dijkstra": t_dij * 1e3}
     if gpu_dist is not None:
         same = [np.array_equal(np.asarray(r[0]).view(np.uint32), gpu_dist[i].view(np.uint32))
                 for i, r in enumerate(res)]
@@ -405,30 +536,21 @@ def cpu_baseline(wl, budget_s: float = 20.0, gpu_dist=None):
 
 # ------------------------------------------------- batched and differentiable
 
-def _time(fn, reps=3, warm=1):
-    import torch
-    for _ in range(warm):
-        fn()
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(reps):
-        fn()
-    e1.record()
-    torch.cuda.synchronize()
-    return e0.elapsed_time(e1) / reps / 1e3
+def _time(fn, reps=3, warm=1, flush=None):
+    """Mean CUDA-event seconds per call (see timed_calls)."""
+    return float(timed_calls(fn, reps, flush=flush, warm=warm).mean())
 
 
-def run_batched(args):
-    """Pattern 2: (a) 1024 sources of an R-MAT s18 graph in batched launches
-    (dawn_msssp) vs a loop of single-source solves; (b) 64 uneven ER graphs
-    solved as one multi-root forest on their disjoint union
-    (dawn_sssp_roots) vs a loop of per-graph solves."""
+ALG_RULE = "16 B per frontier vertex + 12 B per scanned edge + 12 B per update"
+
+
+def leg_msssp(args, device=0):
+    """Pattern 2a: the 1024 sources of an R-MAT s18 graph in batched
+    launches (dawn_msssp) vs a loop of single-source solves, each arm in the
+    launch shape the autotuner picks for it."""
     import torch
     import graphgen as gg
     import paper_2306_07872_gb300 as dawn
-    out = {}
     wl = gg.rmat_u32(18, 16, nsrc=1024, seed=0)
     g = dawn.Graph(wl.row_ptr, wl.col, wl.weights)
     src = torch.from_numpy(wl.sources).cuda()
@@ -436,42 +558,63 @@ def run_batched(args):
     dist = torch.empty((k, wl.n), dtype=torch.uint32, device="cuda")
     par = torch.empty((k, wl.n), dtype=torch.int32, device="cuda")
     dawn.dawn_reserve(g.handle, k)
+    flush_needed, l2note = l2_rule(wl.n, wl.m, l2_bytes(device))
+    flush = L2Flush(device) if flush_needed else None
     tune_batch = None if args.no_tune else g.autotune(wl.sources, mode="msssp", reps=2)
-    t_batch = _time(lambda: dawn.dawn_msssp(g.handle, src, dist, par))
-    g.check()
-    st = g.stats()  # summed over the launches of the last call
-    rows_host = dist[:64].cpu().numpy()
     srcs = [int(x) for x in wl.sources]
-    # the loop arm gets its own tuned launch shape
-    tune_loop = None if args.no_tune else g.autotune(wl.sources[:8], mode="sssp", reps=2)
+
     def loop():
         for i, s_ in enumerate(srcs):
             dawn.dawn_sssp(g.handle, s_, dist[i], par[i], None)
-    t_loop = _time(loop)
-    g.check()
-    out["msssp_rmat18_1024"] = {"batched_s": t_batch, "loop_s": t_loop, "speedup": t_loop / t_batch,
-                                "gteps_batched": k * wl.e_wcc / t_batch / 1e9,
-                                "gteps_loop": k * wl.e_wcc / t_loop / 1e9,
-                                "edges_scanned_per_instance": st["edges_scanned"] / k,
-                                "updates_per_instance": st["updates"] / k,
-                                "tuning_batched": tune_batch, "tuning_loop": tune_loop,
-                                "roofline": roofline_entry(bytes_alg(st), t_batch, "govm_kernel (1024 instances)",
-                                                           "16 B per frontier vertex + 12 B per scanned edge + "
-                                                           "12 B per update, summed over the instances")}
+    # the loop arm gets its own tuned launch shape; both shapes are applied
+    # in turn inside the one clocked region
+    tune_loop = None if args.no_tune else g.autotune(wl.sources[:8], mode="sssp", reps=2)
+    def use(t):
+        if t:
+            dawn.dawn_set_option(g.handle, dawn.DAWN_OPT_CTAS_PER_SM, t["ctas_per_sm"])
+            dawn.dawn_set_option(g.handle, dawn.DAWN_OPT_GRID_BLOCKS, t["grid_blocks"])
+            dawn.dawn_set_option(g.handle, dawn.DAWN_OPT_BATCH, t["batch"])
+            dawn.dawn_set_option(g.handle, dawn.DAWN_OPT_SMALL_PATH, t["small_path"])
+    with Clocks(device) as clk:
+        use(tune_batch)
+        tb = timed_calls(lambda: dawn.dawn_msssp(g.handle, src, dist, par), 5, flush=flush)
+        g.check()
+        st = g.stats()  # summed over the launches of the last call
+        rows_host = dist[:64].cpu().numpy()
+        use(tune_loop)
+        tl = timed_calls(loop, 3, flush=flush)
+        g.check()
+    t_batch, t_loop = float(tb.mean()), float(tl.mean())
+    out = {"batched_s": t_batch, "loop_s": t_loop, "speedup": t_loop / t_batch,
+           "gteps_batched": k * wl.e_wcc / t_batch / 1e9, "gteps_loop": k * wl.e_wcc / t_loop / 1e9,
+           "edges_scanned_per_instance": st["edges_scanned"] / k, "updates_per_instance": st["updates"] / k,
+           "tuning_batched": tune_batch, "tuning_loop": tune_loop, "clocks": clk.summary(), "l2": l2note,
+           "config": {"workload": wl.name, "n": wl.n, "m": wl.m, "e_wcc": wl.e_wcc, "sources": k,
+                      "timed_calls": {"batched": len(tb), "loop": len(tl)}},
+           "roofline": roofline_entry(bytes_alg(st), t_batch, "govm_kernel (1024 instances)",
+                                      ALG_RULE + ", summed over the instances")}
     if not args.no_cpu:
-        out["msssp_rmat18_1024"]["cpu_baseline"] = cpu_leg_sources(wl, rows_host, args.cpu_budget)
+        out["cpu_baseline"] = cpu_leg_sources(wl, rows_host, args.cpu_budget)
     del dist, par
     g.close()
     torch.cuda.empty_cache()
+    return out
+
+
+def leg_roots(args, device=0):
+    """Pattern 2b: 64 uneven ER graphs solved as one multi-root forest on
+    their disjoint union (dawn_sssp_roots) vs a loop of per-graph solves."""
+    import torch
+    import graphgen as gg
+    import paper_2306_07872_gb300 as dawn
     wb = gg.er_batch(count=64, seed=0)
     gu = dawn.Graph(wb.row_ptr, wb.col, wb.weights)
     roots = torch.from_numpy(wb.sources).cuda()
     du = torch.empty(wb.n, dtype=torch.uint32, device="cuda")
     pu = torch.empty(wb.n, dtype=torch.int32, device="cuda")
+    flush_needed, l2note = l2_rule(wb.n, wb.m, l2_bytes(device))
+    flush = L2Flush(device) if flush_needed else None
     tune_roots = None if args.no_tune else gu.autotune(wb.sources, mode="roots", reps=2)
-    t_roots = _time(lambda: dawn.dawn_sssp_roots(gu.handle, roots, du, pu))
-    gu.check()
-    st_roots = gu.stats()
     offs = wb.extra["offsets"]
     parts = []
     for i in range(64):
@@ -483,29 +626,43 @@ def run_batched(args):
             parts[-1].autotune([0], mode="sssp", reps=1)
     outs = [(torch.empty(p_.n, dtype=torch.uint32, device="cuda"), torch.empty(p_.n, dtype=torch.int32, device="cuda"))
             for p_ in parts]
+
     def loop2():
         for p_, (d_, pp_) in zip(parts, outs):
             dawn.dawn_sssp(p_.handle, 0, d_, pp_, None)
-    t_loop2 = _time(loop2)
-    for p_ in parts:
-        p_.check()
-    out["roots_er64"] = {"one_launch_s": t_roots, "loop_s": t_loop2, "speedup": t_loop2 / t_roots,
-                         "gteps_one_launch": wb.m / t_roots / 1e9, "gteps_loop": wb.m / t_loop2 / 1e9,
-                         "n": wb.n, "m": wb.m, "tuning_one_launch": tune_roots,
-                         "roofline": roofline_entry(bytes_alg(st_roots), t_roots, "govm_kernel (multi-root forest)",
-                                                    "16 B per frontier vertex + 12 B per scanned edge + "
-                                                    "12 B per update")}
+    one = lambda: dawn.dawn_sssp_roots(gu.handle, roots, du, pu)
+    with Clocks(device) as clk:
+        tr = timed_calls(one, reps_for(one, 1.0, lo=5, hi=200), flush=flush)
+        gu.check()
+        st_roots = gu.stats()
+        tl = timed_calls(loop2, reps_for(loop2, 1.0, lo=3, hi=100), flush=flush)
+        for p_ in parts:
+            p_.check()
+    t_roots, t_loop2 = float(tr.mean()), float(tl.mean())
+    out = {"one_launch_s": t_roots, "loop_s": t_loop2, "speedup": t_loop2 / t_roots,
+           "gteps_one_launch": wb.m / t_roots / 1e9, "gteps_loop": wb.m / t_loop2 / 1e9,
+           "tuning_one_launch": tune_roots, "clocks": clk.summary(), "l2": l2note,
+           "config": {"workload": wb.name, "n": wb.n, "m": wb.m, "graphs": 64,
+                      "gteps_edges": "all m edges of the union (every graph is solved from its root)",
+                      "timed_calls": {"one_launch": len(tr), "loop": len(tl)}},
+           "roofline": roofline_entry(bytes_alg(st_roots), t_roots, "govm_kernel (multi-root forest)", ALG_RULE)}
     if not args.no_cpu:
-        out["roots_er64"]["cpu_baseline"] = cpu_leg_roots(wb, du.cpu().numpy())
+        out["cpu_baseline"] = cpu_leg_roots(wb, du.cpu().numpy())
     for p_ in parts:
         p_.close()
     gu.close()
+    torch.cuda.empty_cache()
     return out
 
 
-def run_diff(args):
-    """Pattern 3 on R-MAT s16 fp32: plain solve, forward (weights loaded +
-    solve saving the parent tree) and forward + backward."""
+def run_batched(args):
+    return {"msssp_rmat18_1024": leg_msssp(args), "roots_er64": leg_roots(args)}
+
+
+def leg_diff(args, device=0):
+    """Pattern 3 on R-MAT s16 fp32: plain solve, forward + backward through
+    the C ABI, and forward (weights loaded + solve saving the parent tree)
+    and forward + backward through torch.autograd."""
     import torch
     import graphgen as gg
     import paper_2306_07872_gb300 as dawn
@@ -516,48 +673,104 @@ def run_diff(args):
     cf = torch.from_numpy(wl.extra["coef"]).float().cuda()
     dist = torch.empty(wl.n, dtype=torch.float32, device="cuda")
     pe = torch.empty(wl.n, dtype=torch.int32, device="cuda")
-    t_plain = _time(lambda: dawn.dawn_sssp(g.handle, 0, dist, None, pe), reps=20, warm=3)
-    def fwd():
-        return dawn.DawnSSSP.apply(w, g, 0)
-    t_fwd = _time(fwd, reps=20, warm=3)
-    def fwd_bwd():
-        ww = w.clone().requires_grad_(True)
-        d = dawn.DawnSSSP.apply(ww, g, 0)
-        (d[tg] * cf).sum().backward()
-    t_fb = _time(fwd_bwd, reps=20, warm=3)
-    def fwd_bwd_nosync():  # status read after the loop, not per forward
-        ww = w.clone().requires_grad_(True)
-        d = dawn.DawnSSSP.apply(ww, g, 0, False)
-        (d[tg] * cf).sum().backward()
-    t_fb_ns = _time(fwd_bwd_nosync, reps=20, warm=3)
-    g.check()
     grad_dist = torch.zeros(wl.n, dtype=torch.float32, device="cuda")
     grad_dist[tg] = cf
     grad_w = torch.empty(wl.m, dtype=torch.float32, device="cuda")
-    t_bwd = _time(lambda: dawn.dawn_sssp_backward(g.handle, pe, grad_dist, grad_w), reps=20, warm=3)
+    flush_needed, l2note = l2_rule(wl.n, wl.m, l2_bytes(device))
+    flush = L2Flush(device) if flush_needed else None
+    ww = w.clone().requires_grad_(True)
+
+    def plain():
+        dawn.dawn_sssp(g.handle, 0, dist, None, pe)
+
+    def fwd():
+        return dawn.DawnSSSP.apply(w, g, 0)
+
+    def fwd_bwd():
+        ww.grad = None
+        d = dawn.DawnSSSP.apply(ww, g, 0)
+        (d[tg] * cf).sum().backward()
+
+    def fwd_bwd_nosync():  # status read after the loop, not per forward
+        ww.grad = None
+        d = dawn.DawnSSSP.apply(ww, g, 0, False)
+        (d[tg] * cf).sum().backward()
+
+    def bwd():
+        dawn.dawn_sssp_backward(g.handle, pe, grad_dist, grad_w)
+
     def c_abi_fwd_bwd():
         dawn.dawn_sssp(g.handle, 0, dist, None, pe)
         dawn.dawn_sssp_backward(g.handle, pe, grad_dist, grad_w)
-    t_cfb = _time(c_abi_fwd_bwd, reps=20, warm=3)
+    times = {}
+    with Clocks(device) as clk:
+        for name, fn in (("plain_sssp_s", plain), ("backward_kernel_s", bwd), ("c_abi_forward_backward_s", c_abi_fwd_bwd),
+                         ("autograd_forward_s", fwd), ("autograd_forward_backward_s", fwd_bwd),
+                         ("autograd_forward_backward_nosync_s", fwd_bwd_nosync)):
+            times[name] = float(np.median(timed_calls(fn, reps_for(fn, 0.4, lo=20, hi=2000), flush=flush, warm=3)))
+        g.check()
+    dawn.dawn_sssp(g.handle, 0, dist, None, pe)
+    bwd()
     g.check()
-    g.close()
     tree = int((pe >= 0).sum().item())
     b_bw = 8 * wl.n + 4 * wl.m + 12 * tree
-    res = {"diff_rmat16_f32": {"plain_sssp_s": t_plain, "c_abi_forward_backward_s": t_cfb,
-                                "c_abi_fb_over_plain": t_cfb / t_plain, "backward_kernel_s": t_bwd,
-                                "autograd_forward_s": t_fwd, "autograd_forward_backward_s": t_fb,
-                                "autograd_fb_over_plain": t_fb / t_plain,
-                                "autograd_forward_backward_nosync_s": t_fb_ns,
-                                "autograd_fb_nosync_over_plain": t_fb_ns / t_plain, "n": wl.n, "m": wl.m,
-                                "tree_edges": tree,
-                                "roofline_backward": roofline_entry(
-                                    b_bw, t_bwd, "bw_count_kernel + bw_walk_kernel",
-                                    "8 B per vertex (dL/d dist, parent edge) + 4 B per edge (dL/dw written, "
-                                    "zeros included) + 12 B per tree edge (tail lookup, accumulator "
-                                    "read-modify-write)")}}
+    res = dict(times)
+    res.update({"c_abi_fb_over_plain": times["c_abi_forward_backward_s"] / times["plain_sssp_s"],
+                "autograd_fb_over_plain": times["autograd_forward_backward_s"] / times["plain_sssp_s"],
+                "autograd_fb_nosync_over_plain": times["autograd_forward_backward_nosync_s"] / times["plain_sssp_s"],
+                "timing": "median of per-call CUDA events", "clocks": clk.summary(), "l2": l2note,
+                "config": {"workload": wl.name, "n": wl.n, "m": wl.m, "source": 0, "targets": len(wl.extra["targets"]),
+                           "tree_edges": tree},
+                "roofline": roofline_entry(
+                    b_bw, times["backward_kernel_s"], "bw_count_kernel + bw_walk_kernel",
+                    "8 B per vertex (dL/d dist, parent edge) + 4 B per edge (dL/dw written, zeros included) + "
+                    "12 B per tree edge (tail lookup, accumulator read-modify-write)")})
     if not args.no_cpu:
-        res["diff_rmat16_f32"]["cpu_baseline"] = cpu_leg_diff(wl, grad_dist.cpu().numpy(), grad_w.cpu().numpy())
+        res["cpu_baseline"] = cpu_leg_diff(wl, grad_dist.cpu().numpy(), grad_w.cpu().numpy())
+    g.close()
+    torch.cuda.empty_cache()
     return res
+
+
+def run_diff(args):
+    return {"diff_rmat16_f32": leg_diff(args)}
+
+
+def leg_grid(args, device=0):
+    """C3: the 2048^2 fp32 grid with 1 % shortcuts, 16 sources each solved as
+    its own SSSP (many GOVM steps with small frontiers)."""
+    wl = make_workload("grid")
+    res = run_sssp_bench(args, wl, device, 1, 0, steps=min(args.steps, 5))
+    out = {"gteps": res["gteps"], "gteps_median": res["gteps_median"], "launch_ms_mean": res["launch_ms_mean"],
+           "steps_timed": res["steps"], "govm_steps_mean": res["steps_mean"], "mu_gpu": res["mu_gpu"],
+           "edges_scanned_over_e_wcc": res["edges_scanned_mean"] / wl.e_wcc,
+           "us_per_govm_step": res["launch_ms_mean"] * 1e3 / max(res["steps_mean"], 1.0),
+           "clocks": res["clocks"], "l2": res["l2"], "tuning": res["tuning"],
+           "config": {"workload": wl.name, "n": wl.n, "m": wl.m, "e_wcc": wl.e_wcc, "sources_per_step": len(wl.sources),
+                      "timed_steps": res["steps"]},
+           "roofline": {**roofline_entry(res["b_alg_mean"], res["launch_ms_mean"] / 1e3, "govm_kernel", ALG_RULE),
+                        "traffic": recorded_traffic(wl.name), "frac_b_min": res["achieved_gbs_b_min"] / measured_peak()[0]}}
+    if not args.no_cpu:
+        out["cpu_baseline"] = cpu_baseline(wl, args.cpu_budget, res["dist_host"], single_core=False)
+    return out
+
+
+def gather_ceiling(device, n_rows: int, count: int = 1 << 26):
+    """Random 8-byte gathers per second by a stock torch kernel
+    (index_select of int64 rows at random int32 indices) from an array of
+    n_rows rows, the size of the solver's packed state: the rate of the
+    random L2 requests that every scanned edge makes."""
+    import torch
+    x = torch.arange(n_rows, dtype=torch.int64, device=device)
+    gen = torch.Generator(device=device)
+    gen.manual_seed(7)
+    idx = torch.randint(0, n_rows, (count,), dtype=torch.int32, device=device, generator=gen)
+    out = torch.empty(count, dtype=torch.int64, device=device)
+    t = timed_calls(lambda: torch.index_select(x, 0, idx, out=out), 5, warm=2)
+    best = float(t.min())
+    return {"gathers_per_s": count / best, "array_mb": 8 * n_rows / 1e6, "count": count,
+            "kernel": "torch.index_select (int64 rows, int32 indices)", "best_of": len(t),
+            "note": "each gather also streams a 4 B index in and an 8 B result out"}
 
 
 def cpu_leg_sources(wl, gpu_rows, budget_s: float):
@@ -684,7 +897,10 @@ def run_apsp(args):
     src = torch.arange(n, dtype=torch.int32, device="cuda")
     dist = torch.empty((n, n), dtype=torch.uint32, device="cuda")
     tuning = None if args.no_tune else g.autotune(np.arange(n, dtype=np.int32), mode="msssp", reps=1)
-    t = _time(lambda: dawn.dawn_msssp(g.handle, src, dist, None), reps=2, warm=1)
+    flush_needed, l2note = l2_rule(n, len(cl), l2_bytes(0))
+    with Clocks(0) as clk:
+        t = _time(lambda: dawn.dawn_msssp(g.handle, src, dist, None), reps=3, warm=1,
+                  flush=L2Flush(0) if flush_needed else None)
     g.check()
     st = g.stats()  # summed over all launches of the call
     scanned = st["edges_scanned"]
@@ -700,7 +916,8 @@ def run_apsp(args):
         rule = "16 B per frontier vertex + 12 B per scanned edge + 12 B per update, summed over the sources"
     return {"apsp_rmat14": {"n": n, "m": len(cl), "s_wcc": s_wcc, "e_wcc": e_wcc, "seconds": t,
                             "gteps": n * e_wcc / t / 1e9, "edges_scanned": scanned,
-                            "mu_work": scanned / (s_wcc * e_wcc), "tuning": tuning,
+                            "mu_work": scanned / (s_wcc * e_wcc), "tuning": tuning, "clocks": clk.summary(),
+                            "l2": l2note,
                             "roofline": roofline_entry(b_dev, t, "govm_small_kernel" if small else "govm_kernel",
                                                        rule)}}
 
@@ -817,8 +1034,7 @@ def main_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": wl.wtype, "data": "synthetic",
             "config": {"workload": wl.name, "n": wl.n, "m": wl.m, "e_wcc": wl.e_wcc, "s_wcc": wl.s_wcc,
                        "sources_per_step": len(wl.sources) * world, "parallelism": f"replicas{world}",
-                       "l2": "inputs larger than L2 (CSR col+w %.0f MB > 129 MB); no flush" %
-                             ((wl.col.nbytes + wl.weights.nbytes) / 1e6)},
+                       "l2": res["l2"]},
             "roofline": {"bound": "hbm", "achieved": res["achieved_gbs"], "peak": peak, "unit": "GB/s",
                          "frac": res["achieved_gbs"] / peak, "traffic": recorded_traffic(wl.name),
                          "peak_kind": f"{peak_kind} copy bandwidth", "kernel": "govm_kernel",
@@ -826,6 +1042,7 @@ def main_ours(args):
                          "frac_of_8000": res["achieved_gbs"] / 8000.0,
                          "b_min_per_launch": res["b_min_mean"],
                          "frac_b_min": res["achieved_gbs_b_min"] / peak},
+            "gather_ceiling": None,
             "gteps_median": res["gteps_median"], "gteps_hmean_per_launch": res["gteps_hmean"],
             "solver": {"steps_mean": res["steps_mean"], "updates_mean": res["updates_mean"], "mu_gpu": res["mu_gpu"],
                        "edges_scanned_mean": res["edges_scanned_mean"],
@@ -833,6 +1050,23 @@ def main_ours(args):
             "e2e": e2e, "gpu_launches": res["launches"], "clocks": res["clocks"], "cpu_baseline": cpu,
             "tuning": res["tuning"],
         }
+        if world == 1 and not args.no_legs:
+            # the random-gather rate of this GPU, and the rate of state reads
+            # (one per scanned edge, one per frontier vertex) the solver made
+            gc = gather_ceiling(device, wl.n)
+            req = (res["edges_scanned_mean"] + res["frontier_sum_mean"]) / (res["launch_ms_mean"] / 1e3)
+            line["gather_ceiling"] = gc
+            line["roofline"]["state_reads_per_s"] = req
+            line["roofline"]["frac_of_gather_ceiling"] = req / gc["gathers_per_s"]
+        if world == 1 and args.workload == "rmat22" and not args.no_legs:
+            # the rest of the metric: high-diameter, batched and
+            # differentiable forms beside the plain solver, each with its own
+            # clocks, roofline and oracle leg
+            for key, fn in (("grid_2048_f32", leg_grid), ("msssp_rmat18_1024", leg_msssp),
+                            ("roots_er64", leg_roots), ("diff_rmat16_f32", leg_diff)):
+                t = time.time()
+                line[key] = fn(args, device)
+                log(f"[bench] leg {key} done in {time.time() - t:.1f} s")
         print(json.dumps(line), flush=True)
     elif args.workload in ("batched", "diff", "mu", "apsp", "gsvm"):
         if world > 1 and rank != 0:
@@ -856,6 +1090,8 @@ def build_parser() -> argparse.ArgumentParser:
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch shape (no autotuning)")
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--sources", type=int, default=0, help="limit sources per step (profiling runs)")
+    ap.add_argument("--no-legs", action="store_true",
+                    help="only the R-MAT s22 line: skip the grid, batched and backward legs and the gather ceiling")
     return ap
 
 

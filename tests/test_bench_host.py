@@ -107,3 +107,21 @@ def test_profile_commands_run_committed_files_with_current_flags():
         ncu_lines = [l for l in text.replace("\\\n", " ").splitlines() if re.search(r"(^|&&)\s*ncu\s", l.strip())]
         for line in ncu_lines:
             assert "--clock-control none" in line, (f, line)
+
+
+def test_l2_rule_and_clock_summary():
+    l2 = 132 * 2 ** 20
+    flush, note = bench.l2_rule(1024, 8192, l2)  # the tiny ER graph: 69 KB
+    assert flush and "fits in L2" in note and "0.1 MB" in note
+    flush, note = bench.l2_rule(1 << 22, 65_243_778, l2)  # R-MAT s22: 539 MB
+    assert not flush and "larger than L2" in note and "539 MB" in note
+    assert bench.graph_bytes(10, 7) == 4 * 11 + 8 * 7
+    lines = ["0, 1500, 2070, 300.1, 0x0, Not Active, Not Active, Not Active, Not Active, 0",
+             "0, 2070, 2070, 900.5, 0x4, Not Active, Not Active, Not Active, Active, 100",
+             "0, 2060, 2070, 901.0, 0x0, Not Active, Not Active, Not Active, Not Active, 97"]
+    s = bench.clocks_summary(lines)
+    assert s["sm_mhz"] == 2065 and s["sm_max_mhz"] == 2070 and s["samples"] == 3
+    assert s["samples_under_load"] == 2 and s["reasons"] == ["sw_power_cap"]
+    assert bench.clocks_summary([])["reasons"] == ["unsampled"]
+    # the older nine-field form (no utilisation) still parses
+    assert bench.clocks_summary([l.rsplit(",", 1)[0] for l in lines])["sm_mhz"] == 2060

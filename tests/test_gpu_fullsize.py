@@ -2,8 +2,10 @@
 benchmark times (the one dawn_autotune picks for the workload, tuned the
 same way before the solves).  Every source's output passes the oracle's optimality
 certificate (dist is the exact (min, fl(+)) fixpoint and parent_edge a
-valid shortest-path forest); a sample of sources is also compared bit for bit
-with the oracle's Dijkstra and lowest-index parent rule."""
+valid shortest-path forest), and every source's parents are compared exactly
+with the oracle's lowest-index parent rule applied to those certified
+distances; a sample of sources is also compared bit for bit with the oracle's
+Dijkstra."""
 from concurrent.futures import ThreadPoolExecutor
 
 import numpy as np
@@ -32,6 +34,18 @@ def certify_all(wl, roots_list, dists, pes, threads=16):
     assert not bad, f"certificate failures (index, (code, where)): {bad[:5]}"
 
 
+def parents_all(wl, roots_list, dists, pes, threads=16):
+    """Every instance's parent edges equal the oracle's lowest-index rule on
+    its (certified) distances."""
+    def one(i):
+        ref = oracle.parent_edges(wl.row_ptr, wl.col, wl.weights, roots_list[i], dists[i])
+        return bool(np.array_equal(pes[i], ref))
+    with ThreadPoolExecutor(threads) as ex:
+        res = list(ex.map(one, range(len(roots_list))))
+    bad = [i for i, ok in enumerate(res) if not ok]
+    assert not bad, f"parent edges differ from the lowest-index rule for instances {bad[:10]}"
+
+
 def exact(wl, roots, d, pe):
     d_ref = oracle.dijkstra(wl.row_ptr, wl.col, wl.weights, roots)
     assert np.array_equal(np.asarray(d).view(np.uint32), d_ref.view(np.uint32))
@@ -54,6 +68,7 @@ def test_rmat22_u32_64_sources(dawn):
     g.autotune(wl.sources[:8], mode="sssp", reps=2)
     ds, pes = solve_all(g, wl.sources)
     certify_all(wl, [int(s) for s in wl.sources], ds, pes)
+    parents_all(wl, [int(s) for s in wl.sources], ds, pes)
     for i in (0, 41):
         exact(wl, int(wl.sources[i]), ds[i], pes[i])
 
@@ -64,6 +79,7 @@ def test_grid2048_f32_16_sources(dawn):
     g.autotune(wl.sources[:8], mode="sssp", reps=2)
     ds, pes = solve_all(g, wl.sources)
     certify_all(wl, [int(s) for s in wl.sources], ds, pes)
+    parents_all(wl, [int(s) for s in wl.sources], ds, pes)
     exact(wl, int(wl.sources[3]), ds[3], pes[3])
 
 
@@ -74,17 +90,27 @@ def test_rmat18_msssp_1024_sources(dawn):
     dist, par = g.msssp(wl.sources)
     dist = dist.cpu().numpy()
     par = par.cpu().numpy()
-    pick = list(range(0, 1024, 32))
-    # parent vertices -> parent edges are not stored by msssp; recompute the
-    # rule from the oracle for the sampled instances and compare
-    for i in pick[:4]:
-        d_ref = oracle.dijkstra(wl.row_ptr, wl.col, wl.weights, int(wl.sources[i]))
+    # every instance: parent edges by the oracle's rule on the GPU's
+    # distances, certified (exact fixpoint, valid forest), and the GPU's
+    # parent vertices equal to the tails of those edges
+    roots = [int(x) for x in wl.sources]
+    tails = oracle.edge_tails(wl.row_ptr)
+
+    def one(i):
+        pe = oracle.parent_edges(wl.row_ptr, wl.col, wl.weights, roots[i], dist[i])
+        code = oracle.certificate(wl.row_ptr, wl.col, wl.weights, roots[i], dist[i], pe)
+        p_ref = np.full(wl.n, -1, np.int32)
+        p_ref[pe >= 0] = tails[pe[pe >= 0]]
+        p_ref[roots[i]] = roots[i]
+        return code[0] == 0 and bool(np.array_equal(par[i], p_ref))
+    with ThreadPoolExecutor(16) as ex:
+        ok = list(ex.map(one, range(len(roots))))
+    bad = [i for i, v in enumerate(ok) if not v]
+    assert not bad, f"instances failing the certificate or the parent rule: {bad[:10]}"
+    # a sample also bit for bit against the oracle's Dijkstra
+    for i in (0, 511, 1023):
+        d_ref = oracle.dijkstra(wl.row_ptr, wl.col, wl.weights, roots[i])
         assert np.array_equal(dist[i], d_ref), i
-        pe_ref = oracle.parent_edges(wl.row_ptr, wl.col, wl.weights, int(wl.sources[i]), d_ref)
-        p_ref = oracle.parent_vertices(wl.row_ptr, int(wl.sources[i]), d_ref, pe_ref, "u32")
-        assert np.array_equal(par[i], p_ref), i
-    pes = [oracle.parent_edges(wl.row_ptr, wl.col, wl.weights, int(wl.sources[i]), dist[i]) for i in pick]
-    certify_all(wl, [int(wl.sources[i]) for i in pick], [dist[i] for i in pick], pes)
 
 
 def test_er_batch_roots(dawn):
