@@ -709,15 +709,38 @@ def leg_diff(args, device=0):
                          ("autograd_forward_backward_nosync_s", fwd_bwd_nosync)):
             times[name] = float(np.median(timed_calls(fn, reps_for(fn, 0.4, lo=20, hi=2000), flush=flush, warm=3)))
         g.check()
+        # the same autograd step (no status read) captured once in a CUDA
+        # graph and replayed: what a training loop that captures its step runs
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            for _ in range(2):
+                fwd_bwd_nosync()
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        ww.grad = None
+        cg = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(cg):
+            d_cap = dawn.DawnSSSP.apply(ww, g, 0, False)
+            (d_cap[tg] * cf).sum().backward()
+        times["autograd_forward_backward_graph_s"] = float(np.median(
+            timed_calls(cg.replay, reps_for(cg.replay, 0.4, lo=20, hi=2000), flush=flush, warm=3)))
+        g.check()
+        grad_graph = ww.grad.detach().clone()
     dawn.dawn_sssp(g.handle, 0, dist, None, pe)
     bwd()
     g.check()
+    # the replayed graph's gradient against the C ABI's (float32 sums in a
+    # varying order: compared relative to the largest value)
+    graph_grad_diff = float((grad_graph - grad_w).abs().max().item() / max(grad_w.abs().max().item(), 1e-30))
     tree = int((pe >= 0).sum().item())
     b_bw = 8 * wl.n + 4 * wl.m + 12 * tree
     res = dict(times)
     res.update({"c_abi_fb_over_plain": times["c_abi_forward_backward_s"] / times["plain_sssp_s"],
                 "autograd_fb_over_plain": times["autograd_forward_backward_s"] / times["plain_sssp_s"],
                 "autograd_fb_nosync_over_plain": times["autograd_forward_backward_nosync_s"] / times["plain_sssp_s"],
+                "autograd_fb_graph_over_plain": times["autograd_forward_backward_graph_s"] / times["plain_sssp_s"],
+                "graph_grad_max_diff_over_max": graph_grad_diff,
                 "timing": "median of per-call CUDA events", "clocks": clk.summary(), "l2": l2note,
                 "config": {"workload": wl.name, "n": wl.n, "m": wl.m, "source": 0, "targets": len(wl.extra["targets"]),
                            "tree_edges": tree},

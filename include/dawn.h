@@ -116,8 +116,15 @@ int dawn_create_graph(int32_t n, int64_t m, const int32_t *row_ptr, const int32_
  *          output and reports DAWN_ERR_INVALID in dawn_status (stream
  *          ordered: issue the solve on the same stream, or order the streams).
  * Every solve checks the verdict of the weights in force, so weights that a
- * synchronous call rejected (the copy has already replaced the old ones) are
+ * synchronous call rejected (they have already replaced the old ones) are
  * refused as well until valid weights are set.
+ * Device weights are read in place by one stream-ordered kernel that checks
+ * them and writes them into the solver's interleaved (column, weight)
+ * array: keep them unchanged until `stream` has passed the call.  Host
+ * weights are first copied to a device staging buffer of 4 bytes per edge,
+ * allocated on the handle's first host-memory call and kept until
+ * dawn_destroy (DAWN_ERR_OOM if that allocation fails; the weights in force
+ * are then unchanged).
  */
 enum { DAWN_WEIGHTS_ON_DEVICE = 1, DAWN_WEIGHTS_DEFER_CHECK = 2 };
 int dawn_set_weights(dawn_graph g, const void *weights, int flags, void *stream);
@@ -193,8 +200,8 @@ int dawn_sssp_roots(dawn_graph g, const int32_t *roots, int32_t k, void *dist, i
  * that varies from call to call, so the last bits may differ between calls.
  * A parent_edge array that contains a cycle or an edge index outside [0, m)
  * makes the call fail with DAWN_ERR_INVALID in dawn_status().  The first call
- * on a handle allocates 16 bytes per vertex of scratch (make one call before
- * capturing the backward into a CUDA graph).
+ * on a handle allocates 16 bytes per vertex (plus 32) of scratch (make one
+ * call before capturing the backward into a CUDA graph).
  */
 int dawn_sssp_backward(dawn_graph g, const int32_t *parent_edge, const float *grad_dist, float *grad_w,
                        void *stream);
@@ -244,6 +251,23 @@ int dawn_get_stats(dawn_graph g, dawn_stats *out);
  *                          the device (tests the out-of-memory paths); 0 = off
  *   DAWN_OPT_TRACE_STEPS   record up to `value` per-step trace rows in later
  *                          solves (0 = off, the default); allocates
+ *   DAWN_OPT_FRONTIER      how the persistent kernel holds the frontier delta
+ *                          between steps.  DAWN_FRONTIER_QUEUE: compacted
+ *                          into a queue whose out-edges are cut into
+ *                          128-edge tiles (work balanced by edges; two
+ *                          device-wide barriers per step).
+ *                          DAWN_FRONTIER_BITMAP: left in the bitmap of the
+ *                          previous step's marks, from which each warp
+ *                          expands the marked vertices of a range directly
+ *                          (one barrier per step; a row is expanded by one
+ *                          warp, so long rows unbalance it).
+ *                          DAWN_FRONTIER_AUTO (default): the bitmap when no
+ *                          row has more than 128 out-edges, else the queue.
+ *                          Algorithm 1 (DAWN_OPT_GSVM) and launches of
+ *                          several instances (dawn_msssp) always use the
+ *                          queue.
+ *                          Same results; only the time and the step count
+ *                          (which may differ by one) depend on it.
  *   DAWN_OPT_GSVM          1: solve with Algorithm 1 (GSVM, Section 3.2) instead
  *                          of Algorithm 2: every step rescans the out-edges of
  *                          every reached vertex and the loop stops after a
@@ -261,8 +285,10 @@ enum {
   DAWN_OPT_CTAS_PER_SM = 7,
   DAWN_OPT_BATCH = 8,
   DAWN_OPT_TEST_FAIL_ALLOC = 9,
-  DAWN_OPT_SMALL_PATH = 10
+  DAWN_OPT_SMALL_PATH = 10,
+  DAWN_OPT_FRONTIER = 11
 };
+enum { DAWN_FRONTIER_AUTO = 0, DAWN_FRONTIER_QUEUE = 1, DAWN_FRONTIER_BITMAP = 2 };
 enum { DAWN_SMALL_AUTO = 0, DAWN_SMALL_NEVER = 1, DAWN_SMALL_WHEN_STATE_FITS = 2 };
 int dawn_set_option(dawn_graph g, int option, int64_t value);
 
@@ -343,13 +369,13 @@ int dawn_graph_info(dawn_graph g, int32_t *n, int64_t *m, int *wtype);
  * dawn_status(g, 1), dawn_get_stats and dawn_get_trace report this call like
  * any other solve, and dawn_destroy waits for its stream.
  * Options: DAWN_OPT_MAX_STEPS, DAWN_OPT_WAIT_LIMIT_NS, DAWN_OPT_GRID_BLOCKS,
- * DAWN_OPT_CTAS_PER_SM, DAWN_OPT_GSVM, DAWN_OPT_TRACE_STEPS (the trace
- * buffer is allocated when the option is set) and DAWN_OPT_TEST_STALL apply
- * as for dawn_sssp.  DAWN_OPT_SMALL_PATH does not: the small-graph kernel is
+ * DAWN_OPT_CTAS_PER_SM, DAWN_OPT_FRONTIER, DAWN_OPT_GSVM,
+ * DAWN_OPT_TRACE_STEPS (the trace buffer is allocated when the option is
+ * set) and DAWN_OPT_TEST_STALL apply as for dawn_sssp.  DAWN_OPT_SMALL_PATH does not: the small-graph kernel is
  * never used, so the results are the same but the time may differ.
- * Limit: the workspace takes R(64) + R(16) + R(8 n) + R(4 ceil(n / 32)) +
+ * Limit: the workspace takes R(256) + R(16) + R(8 n) + R(8 ceil(n / 32)) +
  * R(16 n) + R(4 (floor(m / 128) + 2)) bytes, where R(x) rounds x up to a
- * multiple of 256 (about 24.125 bytes per vertex plus 4 bytes per 128 edges
+ * multiple of 256 (about 24.25 bytes per vertex plus 4 bytes per 128 edges
  * plus at most 1.5 KB; with m = 16 n, up to about 1.35 M vertices); a graph
  * whose workspace exceeds 32 MiB (33,554,432 bytes) is rejected with
  * DAWN_ERR_INVALID before anything is enqueued.

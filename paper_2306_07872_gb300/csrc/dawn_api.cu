@@ -22,7 +22,8 @@ struct dawn_graph_s {
   int sms = 0;
   int32_t *row_ptr = nullptr;
   int32_t *col = nullptr;   // staging copy of the columns (freed after interleaving)
-  uint32_t *w = nullptr;    // weight bits as given (kept for dawn_set_weights)
+  uint32_t *w = nullptr;    // staging copy of host weights (freed after creation; dawn_set_weights
+                            // allocates it again on its first host-memory call)
   uint2 *cw = nullptr;      // (column, weight bits) per edge: the array the solver streams
   int32_t *src = nullptr;
   unsigned long long *trace = nullptr;
@@ -36,11 +37,15 @@ struct dawn_graph_s {
   unsigned long long *tails = nullptr;
   int64_t words = 0, tiles_cap = 0;
   DeviceCtl *ctl = nullptr;
-  unsigned *vflags = nullptr;  // validation flags [0] and max weight [1]
-  // backward scratch (allocated by the first dawn_sssp_backward)
-  float *bw_acc = nullptr;        // [n] subtree sums of dL/ddist
+  unsigned *vflags = nullptr;  // validation flags [0], max weight [1], max out-degree [2]
+  int32_t max_deg = 0;         // largest out-degree (read back at creation)
+  // backward scratch (one allocation, made by the first dawn_sssp_backward):
+  // bw_edges | inner | rem | par | acc; the first three are cleared per call
+  // by one memset
+  unsigned char *bw_base = nullptr;
+  unsigned long long *bw_edges = nullptr;  // [4] tree edges expected, handled; blocks finished; unused
   int32_t *bw_cnt = nullptr;      // [3n] has-children flags, children still to arrive, tree parents
-  unsigned long long *bw_edges = nullptr;  // [3] tree edges expected, handled; blocks finished
+  float *bw_acc = nullptr;        // [n] subtree sums of dL/ddist
   // options
   int64_t max_steps = 0;
   unsigned long long wait_limit_ns = 4000000000ull;
@@ -51,6 +56,7 @@ struct dawn_graph_s {
   int test_stall = 0;
   int64_t fail_alloc = 0;  // test hook: the fail_alloc-th next workspace allocation fails
   int gsvm = 0;
+  int frontier = 0;     // DAWN_OPT_FRONTIER
   int occupancy[2] = {0, 0};  // co-resident CTAs per SM of the 4- and 5-CTA builds (cached)
   int last_k = 0;
   cudaStream_t last_stream = nullptr;
@@ -64,12 +70,16 @@ __global__ void validate_kernel(const int32_t *row_ptr, const int32_t *col, cons
                                 int wtype, unsigned *flags) {
   const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long gsize = (long long)gridDim.x * blockDim.x;
-  unsigned bad = 0, wmax = 0;
+  unsigned bad = 0, wmax = 0, dmax = 0;
   for (long long v = gtid; v <= n; v += gsize) {
     const int32_t r = row_ptr[v];
     if (v == 0 && r != 0) bad |= kBadRowPtr;
     if (v == n && (int64_t)r != m) bad |= kBadRowPtr;
-    if (v < n && row_ptr[v + 1] < r) bad |= kBadRowPtr;
+    if (v < n) {
+      const int32_t r1 = row_ptr[v + 1];
+      if (r1 < r) bad |= kBadRowPtr;
+      else dmax = max(dmax, (unsigned)(r1 - r));
+    }
   }
   for (long long e = gtid; e < m; e += gsize) {
     if (col) {
@@ -90,10 +100,12 @@ __global__ void validate_kernel(const int32_t *row_ptr, const int32_t *col, cons
   for (int d = 16; d > 0; d >>= 1) {
     bad |= __shfl_xor_sync(0xFFFFFFFFu, bad, d);
     wmax = max(wmax, __shfl_xor_sync(0xFFFFFFFFu, wmax, d));
+    dmax = max(dmax, __shfl_xor_sync(0xFFFFFFFFu, dmax, d));
   }
   if ((threadIdx.x & 31) == 0) {
     if (bad) atomicOr(flags, bad);
     if (wmax) atomicMax(flags + 1, wmax);
+    if (dmax) atomicMax(flags + 2, dmax);
   }
 }
 
@@ -115,6 +127,37 @@ __global__ void interleave_kernel(const int32_t *col, const uint32_t *w, int64_t
   for (long long e = gtid; e < m; e += gsize) {
     if (col) cw[e] = make_uint2((uint32_t)col[e], w[e]);
     else cw[e].y = w[e];
+  }
+}
+
+// New weights (dawn_set_weights) in one pass: each weight is checked as at
+// creation (float32: finite and >= 0; the largest |w| is kept for the
+// overflow bound of integer types) and written into the weight half of the
+// interleaved (column, weight) array.
+__global__ void weights_kernel(const uint32_t *w, int64_t m, int wtype, uint2 *cw, unsigned *flags) {
+  const long long gtid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long gsize = (long long)gridDim.x * blockDim.x;
+  unsigned bad = 0, wmax = 0;
+  for (long long e = gtid; e < m; e += gsize) {
+    const uint32_t x = w[e];
+    if (wtype == DAWN_W_F32) {
+      const float f = __uint_as_float(x);
+      if (!(f >= 0.0f) || isinf(f)) bad |= kBadWeight;  // NaN fails f >= 0
+    } else if (wtype == DAWN_W_I32) {
+      const int32_t y = (int32_t)x;
+      wmax = max(wmax, y < 0 ? (uint32_t)(-(int64_t)y) : (uint32_t)y);  // |w|
+    } else {
+      wmax = max(wmax, x);
+    }
+    cw[e].y = x;
+  }
+  for (int d = 16; d > 0; d >>= 1) {
+    bad |= __shfl_xor_sync(0xFFFFFFFFu, bad, d);
+    wmax = max(wmax, __shfl_xor_sync(0xFFFFFFFFu, wmax, d));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    if (bad) atomicOr(flags, bad);
+    if (wmax) atomicMax(flags + 1, wmax);
   }
 }
 
@@ -252,7 +295,7 @@ void free_workspace(dawn_graph g) {
 int32_t max_chunk(dawn_graph g) {
   const int64_t tiles_cap = g->m / dawn::kTile + 2;
   int64_t by_tiles = (int64_t)0x7FFFFFFF / tiles_cap;
-  const int64_t per_inst = (int64_t)g->n * (8 + 16) + 4 * ((g->n + 31) / 32) + 4 * tiles_cap + 16;
+  const int64_t per_inst = (int64_t)g->n * (8 + 16) + 8 * ((g->n + 31) / 32) + 4 * tiles_cap + 16;
   size_t free_b = 0, total_b = 0;
   int64_t budget = (int64_t)48 << 30;
   if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) budget = std::min<int64_t>(budget, (int64_t)(free_b / 2));
@@ -267,7 +310,7 @@ int ensure_workspace(dawn_graph g, int32_t k) {
   g->tiles_cap = g->m / dawn::kTile + 2;
   const size_t kn = (size_t)k * g->n;
   int rc;
-  if ((rc = halloc(g, &g->state, kn)) || (rc = halloc(g, &g->bitmap, (size_t)k * g->words)) ||
+  if ((rc = halloc(g, &g->state, kn)) || (rc = halloc(g, &g->bitmap, (size_t)2 * k * g->words)) ||
       (rc = halloc(g, &g->queue, kn)) || (rc = halloc(g, &g->tiles, (size_t)k * g->tiles_cap)) ||
       (rc = halloc(g, &g->tails, (size_t)2 * k))) {
     free_workspace(g);
@@ -318,6 +361,14 @@ int small_mode(dawn_graph g) {
   return 0;
 }
 
+// Direct steps (the frontier read from the bitmap, one barrier per step) or
+// queue steps (the frontier compacted into a queue of 128-edge tiles).
+// Direct steps serve single-instance launches (dawn_sssp, dawn_sssp_roots).
+int direct_steps(dawn_graph g, int32_t k) {
+  if (k != 1 || g->gsvm || g->frontier == DAWN_FRONTIER_QUEUE) return 0;
+  return g->frontier == DAWN_FRONTIER_BITMAP || g->max_deg <= dawn::kDirectMaxDegree;
+}
+
 int run_solve(dawn_graph g, const int32_t *seeds, int32_t nseeds, int32_t source, int32_t k, int roots_mode,
               void *dist, int32_t *parent, int32_t *parent_edge, cudaStream_t stream, bool accumulate = false) {
   const int small = small_mode(g);
@@ -349,6 +400,7 @@ int run_solve(dawn_graph g, const int32_t *seeds, int32_t nseeds, int32_t source
   p.wait_limit_ns = g->wait_limit_ns;
   p.test_stall = g->test_stall;
   p.gsvm = g->gsvm;
+  p.direct = direct_steps(g, k);
   p.trace = g->trace;
   p.trace_cap = g->trace_cap;
   p.vflags = g->vflags;
@@ -357,6 +409,7 @@ int run_solve(dawn_graph g, const int32_t *seeds, int32_t nseeds, int32_t source
   if (accumulate) {
     e = cudaMemsetAsync(&g->ctl->bar, 0, sizeof(g->ctl->bar), stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(g->ctl->changed, 0, sizeof(g->ctl->changed), stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g->ctl->marks, 0, sizeof(g->ctl->marks), stream);
   } else {
     e = cudaMemsetAsync(g->ctl, 0, sizeof(DeviceCtl), stream);
   }
@@ -385,13 +438,13 @@ int copy_in(void *dst, const void *src, size_t bytes, int on_device, cudaStream_
 // Runs the validation kernel; with `wait` the verdict is read back and
 // returned, otherwise only the next solve sees it (through GovmParams).
 int validate(dawn_graph g, cudaStream_t stream, bool wait = true) {
-  cudaError_t e = cudaMemsetAsync(g->vflags, 0, 2 * sizeof(unsigned), stream);
+  cudaError_t e = cudaMemsetAsync(g->vflags, 0, 4 * sizeof(unsigned), stream);
   if (e != cudaSuccess) return cuda_fail(e);
   const int64_t work = std::max<int64_t>(g->m, (int64_t)g->n + 1);
   const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((work + 255) / 256, (int64_t)g->sms * 8));
   validate_kernel<<<blocks, 256, 0, stream>>>(g->row_ptr, g->col, g->w, g->n, g->m, g->wtype,
                                                g->vflags);
-  unsigned h[2] = {0, 0};
+  unsigned h[3] = {0, 0, 0};
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e);
   if (!wait) return DAWN_OK;
@@ -399,6 +452,7 @@ int validate(dawn_graph g, cudaStream_t stream, bool wait = true) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
   if (e != cudaSuccess) return cuda_fail(e);
   if (h[0]) return DAWN_ERR_INVALID;
+  g->max_deg = (int32_t)std::min<unsigned>(h[2], 0x7FFFFFFFu);
   const uint32_t lim = weight_limit(g->wtype);
   if (lim && (uint64_t)g->n * (uint64_t)h[1] >= lim) return DAWN_ERR_INVALID;
   return DAWN_OK;
@@ -414,9 +468,7 @@ void release(dawn_graph g) {
   cudaFree(g->src);
   cudaFree(g->ctl);
   cudaFree(g->vflags);
-  cudaFree(g->bw_acc);
-  cudaFree(g->bw_cnt);
-  cudaFree(g->bw_edges);
+  cudaFree(g->bw_base);
   delete g;
 }
 
@@ -475,7 +527,7 @@ int dawn_create_graph(int32_t n, int64_t m, const int32_t *row_ptr, const int32_
   }
   if ((rc = dalloc(&g->row_ptr, (size_t)n + 1)) || (rc = dalloc(&g->col, (size_t)m)) || (rc = dalloc(&g->w, (size_t)m)) ||
       (rc = dalloc(&g->cw, (size_t)m)) ||
-      (rc = dalloc(&g->src, (size_t)m)) || (rc = dalloc(&g->ctl, 1)) || (rc = dalloc(&g->vflags, 2)) ||
+      (rc = dalloc(&g->src, (size_t)m)) || (rc = dalloc(&g->ctl, 1)) || (rc = dalloc(&g->vflags, 4)) ||
       (rc = copy_in(g->row_ptr, row_ptr, ((size_t)n + 1) * 4, inputs_on_device, s)) ||
       (rc = copy_in(g->col, col_idx, (size_t)m * 4, inputs_on_device, s)) ||
       (rc = copy_in(g->w, weights, (size_t)m * 4, inputs_on_device, s)) || (rc = validate(g, s))) {
@@ -494,8 +546,10 @@ int dawn_create_graph(int32_t n, int64_t m, const int32_t *row_ptr, const int32_
     release(g);
     return DAWN_ERR_CUDA;
   }
-  cudaFree(g->col);  // columns now live in cw
+  cudaFree(g->col);  // columns and weights now live in cw
+  cudaFree(g->w);
   g->col = nullptr;
+  g->w = nullptr;
   g->last_stream = s;
   *out = g;
   return DAWN_OK;
@@ -506,15 +560,29 @@ int dawn_set_weights(dawn_graph g, const void *weights, int flags, void *stream)
     return DAWN_ERR_INVALID;
   if (set_device(g)) return DAWN_ERR_CUDA;
   cudaStream_t s = (cudaStream_t)stream;
-  int rc = copy_in(g->w, weights, (size_t)g->m * 4, flags & DAWN_WEIGHTS_ON_DEVICE, s);
-  if (rc) return rc;
+  const uint32_t *src = (const uint32_t *)weights;
+  int rc;
+  if (!(flags & DAWN_WEIGHTS_ON_DEVICE) && g->m > 0) {  // host weights go through a device staging copy
+    if (!g->w && (rc = halloc(g, &g->w, (size_t)g->m))) return rc;
+    if ((rc = copy_in(g->w, weights, (size_t)g->m * 4, 0, s))) return rc;
+    src = g->w;
+  }
   g->last_stream = s;
-  if ((rc = validate(g, s, !(flags & DAWN_WEIGHTS_DEFER_CHECK)))) return rc;
+  cudaError_t e = cudaMemsetAsync(g->vflags, 0, 2 * sizeof(unsigned), s);
+  if (e != cudaSuccess) return cuda_fail(e);
   if (g->m > 0) {
     const int eb = (int)std::max<int64_t>(1, std::min<int64_t>((g->m + 255) / 256, (int64_t)g->sms * 16));
-    interleave_kernel<<<eb, 256, 0, s>>>(nullptr, g->w, g->m, g->cw);
-    if (cudaGetLastError() != cudaSuccess) return DAWN_ERR_CUDA;
+    weights_kernel<<<eb, 256, 0, s>>>(src, g->m, g->wtype, g->cw, g->vflags);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
   }
+  if (flags & DAWN_WEIGHTS_DEFER_CHECK) return DAWN_OK;  // the next solve reads the verdict itself
+  unsigned h[2] = {0, 0};
+  e = cudaMemcpyAsync(h, g->vflags, sizeof(h), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(e);
+  if (h[0]) return DAWN_ERR_INVALID;
+  const uint32_t lim = weight_limit(g->wtype);
+  if (lim && (uint64_t)g->n * (uint64_t)h[1] >= lim) return DAWN_ERR_INVALID;
   return DAWN_OK;
 }
 
@@ -561,20 +629,17 @@ int dawn_sssp_backward(dawn_graph g, const int32_t *parent_edge, const float *gr
   if (g->wtype != DAWN_W_F32) return DAWN_ERR_INVALID;
   if (set_device(g)) return DAWN_ERR_CUDA;
   cudaStream_t s = (cudaStream_t)stream;
-  if (!g->bw_acc) {
-    int rc;
-    if ((rc = halloc(g, &g->bw_acc, (size_t)g->n)) || (rc = halloc(g, &g->bw_cnt, 3 * (size_t)g->n)) ||
-        (rc = halloc(g, &g->bw_edges, 3))) {
-      cudaFree(g->bw_acc);
-      cudaFree(g->bw_cnt);
-      g->bw_acc = nullptr;
-      g->bw_cnt = nullptr;
-      return rc;
-    }
+  const size_t n = (size_t)g->n;
+  if (!g->bw_base) {
+    int rc = halloc(g, &g->bw_base, 32 + 16 * n);
+    if (rc) return rc;
+    g->bw_edges = (unsigned long long *)g->bw_base;
+    g->bw_cnt = (int32_t *)(g->bw_base + 32);  // inner [n], rem [n], par [n]
+    g->bw_acc = (float *)(g->bw_base + 32 + 12 * n);
   }
+  // status word, then the edge counters and the inner / rem flags in one memset
   cudaError_t e = cudaMemsetAsync(g->ctl, 0, sizeof(DeviceCtl), s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(g->bw_cnt, 0, 2 * sizeof(int32_t) * (size_t)g->n, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(g->bw_edges, 0, 3 * sizeof(unsigned long long), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(g->bw_base, 0, 32 + 8 * n, s);
   if (e != cudaSuccess) return cuda_fail(e);
   if (g->m > 0) {
     const int64_t work = std::max<int64_t>(g->m, g->n);
@@ -645,6 +710,10 @@ int dawn_set_option(dawn_graph g, int option, int64_t value) {
       g->fail_alloc = value;
       return DAWN_OK;
     case DAWN_OPT_GSVM: g->gsvm = value != 0; return DAWN_OK;
+    case DAWN_OPT_FRONTIER:
+      if (value < DAWN_FRONTIER_AUTO || value > DAWN_FRONTIER_BITMAP) return DAWN_ERR_INVALID;
+      g->frontier = (int)value;
+      return DAWN_OK;
     case DAWN_OPT_TRACE_STEPS: {
       if (value < 0 || value > (1 << 24)) return DAWN_ERR_INVALID;
       if (set_device(g)) return DAWN_ERR_CUDA;
@@ -754,7 +823,7 @@ extern "C" int dawn_sssp_noalloc(dawn_graph g, int32_t source, void *dist, int32
   const size_t o_ctl = take(sizeof(DeviceCtl));
   const size_t o_tails = take(2 * sizeof(unsigned long long));
   const size_t o_state = take((size_t)g->n * sizeof(unsigned long long));
-  const size_t o_bitmap = take((size_t)words * sizeof(uint32_t));
+  const size_t o_bitmap = take((size_t)2 * words * sizeof(uint32_t));
   const size_t o_queue = take((size_t)g->n * sizeof(uint4));
   const size_t o_tiles = take((size_t)tiles_cap * sizeof(int32_t));
   if (used > kNoAllocScratchBytes) return DAWN_ERR_INVALID;  // graph too large for the fixed scratch
@@ -789,6 +858,7 @@ extern "C" int dawn_sssp_noalloc(dawn_graph g, int32_t source, void *dist, int32
   p.wait_limit_ns = g->wait_limit_ns;
   p.test_stall = g->test_stall;
   p.gsvm = g->gsvm;
+  p.direct = direct_steps(g, 1);
   p.trace = g->trace;  // allocated when the option was set, not here
   p.trace_cap = g->trace_cap;
   p.vflags = g->vflags;

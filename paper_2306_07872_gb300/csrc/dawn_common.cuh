@@ -9,8 +9,11 @@
 //                        in d, so one 64-bit atomicMin updates
 //                        distance and parent edge together and keeps the
 //                        lexicographically smallest (dist, edge) pair.
-//   bitmap  u32 [k][words]   beta of Algorithm 2: vertices whose distance
+//   bitmap  u32 [2][k][words]  beta of Algorithm 2: vertices whose distance
 //                        dropped in the current step (one bit per vertex).
+//                        Direct steps use both halves: the frontier delta
+//                        (the previous step's marks) and this step's marks;
+//                        queue steps use the first.
 //   queue   uint4[k][n]  delta of Algorithm 2, compacted: one entry per
 //                        frontier vertex with an out-edge = (row start,
 //                        offset of its first edge in the frontier's virtual
@@ -42,6 +45,9 @@ constexpr int kMaxInstancesPerLaunch = 1024;  // per-block prefix over instances
 constexpr uint32_t kNoEdge = 0xFFFFFFFFu;      // parent field of sources and unreachable vertices
 constexpr uint32_t kInfKeyU32 = 0xFFFFFFFFu;
 constexpr uint32_t kInfKeyF32 = 0x7F800000u;  // +inf
+// Direct steps are used (DAWN_FRONTIER_AUTO) when no row has more out-edges
+// than this: a warp then expands 32 rows of at most 32 tiles each.
+constexpr int32_t kDirectMaxDegree = 128;
 
 // Control block: barrier, status and counters (zeroed before every launch).
 struct DeviceCtl {
@@ -53,6 +59,9 @@ struct DeviceCtl {
   unsigned long long edges_scanned;
   unsigned long long updates;
   unsigned int changed[3];  // Algorithm 1 only: "a path changed in step t" flags, t mod 3
+  // Direct steps: "a distance strictly dropped in step t" flags, t mod 3, on
+  // a cache line of their own (the barrier counter's line is the hottest).
+  alignas(128) unsigned int marks[3];
 };
 
 struct GovmParams {
@@ -81,6 +90,7 @@ struct GovmParams {
   unsigned long long wait_limit_ns;
   int test_stall;
   int gsvm;                  // 1: run Algorithm 1 (rescan every reached vertex each step)
+  int direct;                // 1: direct steps (frontier read from the bitmap, one barrier per step)
   unsigned long long *trace;  // optional per-step trace [trace_cap][4], null when off
   int32_t trace_cap;
   // Validation verdict of the graph's current weights (written by the

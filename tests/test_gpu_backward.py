@@ -118,7 +118,7 @@ def test_backward_scratch_allocation_failure(dawn):
     dist, _, pe = g.sssp(0, parent=False, parent_edge=True)
     gd = torch.ones(wl.n, dtype=torch.float32, device="cuda")
     gw = torch.empty(wl.m, dtype=torch.float32, device="cuda")
-    g.set_option(dawn.DAWN_OPT_TEST_FAIL_ALLOC, 2)  # the second scratch array
+    g.set_option(dawn.DAWN_OPT_TEST_FAIL_ALLOC, 1)  # the scratch allocation
     with pytest.raises(dawn.DawnError) as e:
         dawn.dawn_sssp_backward(g.handle, pe, gd, gw)
     assert e.value.code == dawn.DAWN_ERR_OOM
@@ -128,3 +128,46 @@ def test_backward_scratch_allocation_failure(dawn):
     c = np.where(np.isfinite(dist.cpu().numpy()), 1.0, 0.0)
     g_ref = oracle.subtree_grad(wl.row_ptr, wl.col, wl.weights, 0, c, parent_edge=pe_np)
     assert np.all(np.abs(gw.cpu().numpy() - g_ref) <= 1e-4 * np.abs(g_ref) + 1e-30)
+
+
+def test_autograd_step_captured_in_cuda_graph(dawn):
+    # forward (weights loaded + solve), loss and backward captured once and
+    # replayed with new weights written into the same tensor: every replay
+    # gives the oracle's distances and gradient for those weights
+    wl = gg.rmat_f32_diff(scale=12, edge_factor=8, ntargets=32, seed=36)
+    g = dawn.Graph(wl.row_ptr, wl.col, wl.weights)
+    ww = torch.from_numpy(wl.weights).cuda().requires_grad_(True)
+    tg = torch.from_numpy(wl.extra["targets"]).long().cuda()
+    cf = torch.from_numpy(wl.extra["coef"]).float().cuda()
+
+    def step():
+        d = dawn.DawnSSSP.apply(ww, g, 0, False)
+        (d[tg] * cf).sum().backward()
+        return d
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):  # warm-up outside capture (the first backward allocates its scratch)
+        for _ in range(2):
+            ww.grad = None
+            step()
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    ww.grad = None
+    cg = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(cg):
+        d_static = step()
+    c = np.zeros(wl.n)
+    c[wl.extra["targets"]] = wl.extra["coef"].astype(np.float32).astype(np.float64)
+    for scale in (1.0, 0.75, 1.25):
+        w_np = (wl.weights * np.float32(scale)).astype(np.float32)
+        with torch.no_grad():
+            ww.copy_(torch.from_numpy(w_np).cuda())
+        cg.replay()
+        torch.cuda.synchronize()
+        g.check()
+        d_ref, _, pe_ref = oracle.sssp(wl.row_ptr, wl.col, w_np, 0)
+        assert np.array_equal(d_static.detach().cpu().numpy().view(np.uint32), d_ref.view(np.uint32))
+        g_ref = oracle.subtree_grad(wl.row_ptr, wl.col, w_np, 0, c, parent_edge=pe_ref)
+        sabs = oracle.subtree_grad(wl.row_ptr, wl.col, w_np, 0, np.abs(c), parent_edge=pe_ref)
+        got = ww.grad.cpu().numpy()
+        assert np.all(np.abs(got - g_ref) <= 1e-4 * np.maximum(np.abs(g_ref), sabs) + 1e-30), scale

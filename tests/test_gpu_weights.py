@@ -107,3 +107,25 @@ def test_autograd_without_sync_matches(dawn):
     assert np.array_equal(grads[0][0].view(np.uint32), grads[1][0].view(np.uint32))
     # the backward sums with float32 atomics, whose order varies between runs
     np.testing.assert_allclose(grads[0][1], grads[1][1], rtol=1e-5, atol=1e-6)
+
+
+def test_host_weights_staging_allocation_failure(dawn):
+    # host weights go through a device staging copy, allocated on the first
+    # such call; a failed allocation leaves the weights in force untouched
+    wl = gg.grid_f32(30, 0.01, nsrc=1, seed=35)
+    g = dawn.Graph(wl.row_ptr, wl.col, wl.weights)
+    s = int(wl.sources[0])
+    w2 = (wl.weights * np.float32(2.0)).astype(np.float32)
+    g.set_option(dawn.DAWN_OPT_TEST_FAIL_ALLOC, 1)
+    with pytest.raises(dawn.DawnError) as e:
+        dawn.dawn_set_weights(g.handle, torch.from_numpy(w2))
+    assert e.value.code == dawn.DAWN_ERR_OOM
+    dist, code = solve_raw(dawn, g, s)
+    assert code == dawn.DAWN_OK
+    assert np.array_equal(dist.cpu().numpy().view(np.uint32),
+                          oracle.dijkstra(wl.row_ptr, wl.col, wl.weights, s).view(np.uint32))
+    dawn.dawn_set_weights(g.handle, torch.from_numpy(w2))  # allocates and copies now
+    dawn.dawn_set_weights(g.handle, torch.from_numpy(w2))  # reuses the staging copy
+    dist, code = solve_raw(dawn, g, s)
+    assert code == dawn.DAWN_OK
+    assert np.array_equal(dist.cpu().numpy().view(np.uint32), oracle.dijkstra(wl.row_ptr, wl.col, w2, s).view(np.uint32))
