@@ -77,6 +77,9 @@ typedef struct {
                             (they enter beta), counted once per step, summed over steps;
                             updates / (reached vertices - sources) is the paper's mu */
   int64_t instances;     /* instances solved by the last call */
+  int64_t edges_skipped; /* frontier out-edges (counted in edges_scanned) that bitmap steps did
+                            not relax because their vertex was marked again earlier in the
+                            same step (DAWN_OPT_SKIP_REMARKED) */
 } dawn_stats;
 
 /*
@@ -268,6 +271,17 @@ int dawn_get_stats(dawn_graph g, dawn_stats *out);
  *                          queue.
  *                          Same results; only the time and the step count
  *                          (which may differ by one) depend on it.
+ *   DAWN_OPT_SKIP_REMARKED 1 (default): in bitmap steps (DAWN_OPT_FRONTIER),
+ *                          a frontier vertex whose distance drops again
+ *                          during a step before its own out-edges are
+ *                          relaxed is not expanded in that step: it is
+ *                          already marked for the next frontier, where it is
+ *                          expanded with a distance no larger, so expanding
+ *                          it now is redundant.  0: every frontier vertex is
+ *                          expanded in its step, as Algorithm 2 lists it.
+ *                          Queue steps and Algorithm 1 (DAWN_OPT_GSVM) never
+ *                          skip.  Same results; counted in
+ *                          dawn_stats.edges_skipped.
  *   DAWN_OPT_GSVM          1: solve with Algorithm 1 (GSVM, Section 3.2) instead
  *                          of Algorithm 2: every step rescans the out-edges of
  *                          every reached vertex and the loop stops after a
@@ -286,7 +300,8 @@ enum {
   DAWN_OPT_BATCH = 8,
   DAWN_OPT_TEST_FAIL_ALLOC = 9,
   DAWN_OPT_SMALL_PATH = 10,
-  DAWN_OPT_FRONTIER = 11
+  DAWN_OPT_FRONTIER = 11,
+  DAWN_OPT_SKIP_REMARKED = 12
 };
 enum { DAWN_FRONTIER_AUTO = 0, DAWN_FRONTIER_QUEUE = 1, DAWN_FRONTIER_BITMAP = 2 };
 enum { DAWN_SMALL_AUTO = 0, DAWN_SMALL_NEVER = 1, DAWN_SMALL_WHEN_STATE_FITS = 2 };

@@ -57,6 +57,7 @@ struct dawn_graph_s {
   int64_t fail_alloc = 0;  // test hook: the fail_alloc-th next workspace allocation fails
   int gsvm = 0;
   int frontier = 0;     // DAWN_OPT_FRONTIER
+  int skip_remarked = 1;  // DAWN_OPT_SKIP_REMARKED
   int occupancy[2] = {0, 0};  // co-resident CTAs per SM of the 4- and 5-CTA builds (cached)
   int last_k = 0;
   cudaStream_t last_stream = nullptr;
@@ -401,6 +402,7 @@ int run_solve(dawn_graph g, const int32_t *seeds, int32_t nseeds, int32_t source
   p.test_stall = g->test_stall;
   p.gsvm = g->gsvm;
   p.direct = direct_steps(g, k);
+  p.skip_remarked = g->skip_remarked && !g->gsvm;  // Algorithm 1's bitmap holds every reached vertex
   p.trace = g->trace;
   p.trace_cap = g->trace_cap;
   p.vflags = g->vflags;
@@ -676,6 +678,7 @@ int dawn_get_stats(dawn_graph g, dawn_stats *out) {
   out->frontier_sum = (int64_t)h.frontier_sum;
   out->edges_scanned = (int64_t)h.edges_scanned;
   out->updates = (int64_t)h.updates;
+  out->edges_skipped = (int64_t)h.edges_skipped;
   out->instances = g->last_k;
   return DAWN_OK;
 }
@@ -710,6 +713,7 @@ int dawn_set_option(dawn_graph g, int option, int64_t value) {
       g->fail_alloc = value;
       return DAWN_OK;
     case DAWN_OPT_GSVM: g->gsvm = value != 0; return DAWN_OK;
+    case DAWN_OPT_SKIP_REMARKED: g->skip_remarked = value != 0; return DAWN_OK;
     case DAWN_OPT_FRONTIER:
       if (value < DAWN_FRONTIER_AUTO || value > DAWN_FRONTIER_BITMAP) return DAWN_ERR_INVALID;
       g->frontier = (int)value;
@@ -859,6 +863,7 @@ extern "C" int dawn_sssp_noalloc(dawn_graph g, int32_t source, void *dist, int32
   p.test_stall = g->test_stall;
   p.gsvm = g->gsvm;
   p.direct = direct_steps(g, 1);
+  p.skip_remarked = g->skip_remarked && !g->gsvm;
   p.trace = g->trace;  // allocated when the option was set, not here
   p.trace_cap = g->trace_cap;
   p.vflags = g->vflags;

@@ -58,6 +58,7 @@ struct DeviceCtl {
   unsigned long long frontier_sum;
   unsigned long long edges_scanned;
   unsigned long long updates;
+  unsigned long long edges_skipped;  // direct steps: frontier out-edges not relaxed (vertex marked again first)
   unsigned int changed[3];  // Algorithm 1 only: "a path changed in step t" flags, t mod 3
   // Direct steps: "a distance strictly dropped in step t" flags, t mod 3, on
   // a cache line of their own (the barrier counter's line is the hottest).
@@ -91,6 +92,7 @@ struct GovmParams {
   int test_stall;
   int gsvm;                  // 1: run Algorithm 1 (rescan every reached vertex each step)
   int direct;                // 1: direct steps (frontier read from the bitmap, one barrier per step)
+  int skip_remarked;         // direct steps: a frontier vertex marked again in its step is expanded in the next one only
   unsigned long long *trace;  // optional per-step trace [trace_cap][4], null when off
   int32_t trace_cap;
   // Validation verdict of the graph's current weights (written by the

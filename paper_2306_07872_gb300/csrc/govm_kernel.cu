@@ -377,12 +377,13 @@ __device__ void build_frontier(const GovmParams &p, unsigned long long *tails_ne
 // Edge phase of one kTile-edge tile of a laid-out edge list: lane handles
 // virtual edges x0 + 32 r + lane (r < kEdgesPerLane) below xend.  wt.own[s]
 // is the entry owning virtual edge x0 + s (unless jone >= 0: then entry jone
-// owns them all), wt.ebase[j] the CSR index of entry j's virtual offset 0 (mod 2^32)
-// and wt.dkey[j] the distance key of entry j's vertex, which fill_keys()
-// writes after the loads are issued (so that in-place key reads still in
-// flight overlap the edge loads).  Every load of the phase is issued before
-// any result is used, so a lane's requests are in flight together.  Returns
-// the lanes' strict-improvement masks (bit r: round r lowered a distance).
+// owns them all), wt.ebase[j] the CSR index of entry j's virtual offset 0
+// (mod 2^32) and wt.dkey[j] the distance key of entry j's vertex, which
+// fill_keys() writes after the loads are issued (so that in-place key reads
+// still in flight overlap the edge loads).  Every load of the phase is
+// issued before any result is used, so a lane's requests are in flight
+// together.  Returns the lanes' strict-improvement masks (bit r: round r
+// lowered a distance).
 template <int WT, typename FillKeys>
 __device__ __forceinline__ unsigned relax_edges(const GovmParams &p, WarpTile &wt, unsigned long long *st,
                                                 uint32_t *bm, uint32_t x0, uint32_t xend, int32_t jone,
@@ -392,26 +393,65 @@ __device__ __forceinline__ unsigned relax_edges(const GovmParams &p, WarpTile &w
   uint32_t eidx[kEdgesPerLane];
   unsigned valid = 0, jpack = 0;  // jpack: each round's owning entry (8 bits each), reused for the keys
   bool bad = false;
+  uint2 cw[kEdgesPerLane];
+  if (jone >= 0) {
+    // One row owns the tile, so its edges are contiguous from e0: each lane
+    // loads two 16-byte (column, weight) pairs from the even-aligned start
+    // (half the load instructions of one pair per edge); when the start is
+    // odd, lane 0's first slot (the edge before the row's part) takes the
+    // tile's last edge instead.
+    const uint32_t e0 = x0 + wt.ebase[jone];
+    const uint32_t cnt = xend - x0;
+    const uint32_t ea = e0 & ~1u;
+    const uint32_t mm = (uint32_t)p.m;
+    jpack = (uint32_t)jone * 0x01010101u;
+    if (lane == 0 && (uint64_t)e0 + cnt > mm) bad = true;
 #pragma unroll
-  for (int r = 0; r < kEdgesPerLane; ++r) {
-    const uint32_t x = x0 + r * 32 + lane;
-    eidx[r] = 0;
-    if (x < xend) {
-      const int32_t j = jone >= 0 ? jone : wt.own[r * 32 + lane];
-      jpack |= (uint32_t)j << (8 * r);
-      const uint32_t e = x + wt.ebase[j];
-      if (e < (uint32_t)p.m) {
-        valid |= 1u << r;
-        eidx[r] = e;
-      } else {
-        bad = true;
+    for (int h = 0; h < 2; ++h) {
+      const uint32_t ep = ea + 2u * (uint32_t)(h * 32 + lane);
+      const bool in0 = ep >= e0 && ep < e0 + cnt && ep < mm;
+      const bool in1 = ep + 1 >= e0 && ep + 1 < e0 + cnt && ep + 1 < mm;
+      uint4 v = make_uint4(0u, 0u, 0u, 0u);
+      if (in1) {
+        v = __ldcs(reinterpret_cast<const uint4 *>(p.cw + ep));
+      } else if (in0) {
+        const uint2 t = __ldcs(p.cw + ep);
+        v.x = t.x;
+        v.y = t.y;
+      }
+      cw[2 * h] = make_uint2(v.x, v.y);
+      cw[2 * h + 1] = make_uint2(v.z, v.w);
+      eidx[2 * h] = ep;
+      eidx[2 * h + 1] = ep + 1;
+      valid |= (in0 ? 1u : 0u) << (2 * h);
+      valid |= (in1 ? 1u : 0u) << (2 * h + 1);
+    }
+    if (lane == 0 && (e0 & 1u) && cnt == (uint32_t)kTile && ea + kTile < mm) {
+      cw[0] = __ldcs(p.cw + ea + kTile);
+      eidx[0] = ea + kTile;
+      valid |= 1u;
+    }
+  } else {  // rows laid end to end: lane takes edges x0 + 32 r + lane, each owned by wt.own[]
+#pragma unroll
+    for (int r = 0; r < kEdgesPerLane; ++r) {
+      const uint32_t x = x0 + r * 32 + lane;
+      eidx[r] = 0;
+      if (x < xend) {
+        const int32_t j = wt.own[r * 32 + lane];
+        jpack |= (uint32_t)j << (8 * r);
+        const uint32_t e = x + wt.ebase[j];
+        if (e < (uint32_t)p.m) {
+          valid |= 1u << r;
+          eidx[r] = e;
+        } else {
+          bad = true;
+        }
       }
     }
-  }
-  uint2 cw[kEdgesPerLane];
 #pragma unroll
-  for (int r = 0; r < kEdgesPerLane; ++r)
-    cw[r] = (valid & (1u << r)) ? __ldcs(p.cw + eidx[r]) : make_uint2(0u, 0u);
+    for (int r = 0; r < kEdgesPerLane; ++r)
+      cw[r] = (valid & (1u << r)) ? __ldcs(p.cw + eidx[r]) : make_uint2(0u, 0u);
+  }
   if (bad) set_status(p.ctl, DAWN_ERR_BOUNDS);
   unsigned long long curst[kEdgesPerLane];
 #pragma unroll
@@ -528,7 +568,7 @@ __device__ __forceinline__ void relax_tile(const GovmParams &p, WarpTile &wt, in
 // Returns whether this warp made any strict improvement (a mark in bn).
 template <int WT>
 __device__ bool direct_step(const GovmParams &p, uint32_t *bm, uint32_t *bn, WarpTile &wt, unsigned long long &marked,
-                            unsigned long long &front, unsigned long long &edges) {
+                            unsigned long long &front, unsigned long long &edges, unsigned long long &skipped) {
   const int lane = threadIdx.x & 31;
   const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -578,13 +618,21 @@ __device__ bool direct_step(const GovmParams &p, uint32_t *bm, uint32_t *bn, War
       }
       uint32_t rs = 0, deg = 0;
       unsigned long long f = ~0ull;
+      bool again = false;
       if (v >= 0 && v < p.n) {
         rs = (uint32_t)__ldg(p.row_ptr + v);
         deg = (uint32_t)__ldg(p.row_ptr + v + 1) - rs;
         f = ld_relaxed_u64(st + v);  // alpha[v] in place, as Algorithm 2 reads it
+        // a vertex marked again in this step is in the next frontier and is
+        // expanded there with a key no larger: not now
+        if (p.skip_remarked) again = (__ldcg(bn + (v >> 5)) >> (v & 31)) & 1u;
       }
       front += deg > 0;
       edges += deg;
+      if (again) {
+        skipped += deg;
+        deg = 0;
+      }
       uint32_t off = deg;  // exclusive prefix of the degrees: lane's first virtual edge
 #pragma unroll
       for (int d = 1; d < 32; d <<= 1) {
@@ -640,6 +688,7 @@ __global__ void __launch_bounds__(kBlockThreads, MINB) govm_kernel(GovmParams p)
   const unsigned long long kInfState = ((unsigned long long)Key<WT>::inf << 32) | kNoEdge;
   const unsigned long long kSourceState = ((unsigned long long)Key<WT>::zero << 32) | kNoEdge;
   unsigned long long updates = 0;  // vertices entering beta, summed over steps
+  unsigned long long skipped = 0;  // direct steps: frontier out-edges not relaxed (their vertex was marked again)
   unsigned long long seeded = 0;   // the seeds' own marks (not path updates)
   if (tid == 0) {
     sh.bar_target = 0;
@@ -718,7 +767,7 @@ __global__ void __launch_bounds__(kBlockThreads, MINB) govm_kernel(GovmParams p)
       const unsigned long long f0 = front, e0 = edges;
       const bool any = direct_step<WT>(p, p.bitmap + (size_t)(step & 1) * p.words,
                                        p.bitmap + (size_t)((step + 1) & 1) * p.words, sh.wt[warp],
-                                       step == 0 ? seeded : updates, front, edges);
+                                       step == 0 ? seeded : updates, front, edges, skipped);
       if (any && lane == 0) sh.any_mark = 1;
       if (p.trace) {  // traced solves keep the cumulative counters current per step
         unsigned long long df = front - f0, de = edges - e0;
@@ -855,6 +904,10 @@ finish:
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) u += __shfl_down_sync(kFull, u, d);
     if (lane == 0 && u) atomicAdd(&ctl->updates, u);
+    unsigned long long sk = skipped;
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) sk += __shfl_down_sync(kFull, sk, d);
+    if (lane == 0 && sk) atomicAdd(&ctl->edges_skipped, sk);
     if (gtid == 0) atomicMax(&ctl->steps, (unsigned long long)step);  // batched calls: the longest launch
   }
 }

@@ -29,6 +29,7 @@ DAWN_OPT_TRACE_STEPS = 5
 DAWN_OPT_GSVM = 6
 DAWN_OPT_CTAS_PER_SM, DAWN_OPT_BATCH, DAWN_OPT_TEST_FAIL_ALLOC, DAWN_OPT_SMALL_PATH = 7, 8, 9, 10
 DAWN_OPT_FRONTIER = 11
+DAWN_OPT_SKIP_REMARKED = 12
 DAWN_FRONTIER_AUTO, DAWN_FRONTIER_QUEUE, DAWN_FRONTIER_BITMAP = 0, 1, 2
 DAWN_SMALL_AUTO, DAWN_SMALL_NEVER, DAWN_SMALL_WHEN_STATE_FITS = 0, 1, 2
 DAWN_TUNE_SSSP, DAWN_TUNE_MSSSP, DAWN_TUNE_ROOTS = 0, 1, 2
@@ -46,7 +47,8 @@ class DawnError(RuntimeError):
 
 
 class _Stats(ctypes.Structure):
-    _fields_ = [(f, ctypes.c_int64) for f in ("steps", "frontier_sum", "edges_scanned", "updates", "instances")]
+    _fields_ = [(f, ctypes.c_int64) for f in ("steps", "frontier_sum", "edges_scanned", "updates", "instances",
+                                              "edges_skipped")]
 
 
 class _Tuning(ctypes.Structure):

@@ -191,3 +191,42 @@ def test_frontier_option_rejects_bad_values(dawn):
         with pytest.raises(dawn.DawnError) as e:
             g.set_option(dawn.DAWN_OPT_FRONTIER, v)
         assert e.value.code == dawn.DAWN_ERR_INVALID
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_skip_remarked_same_results(dawn, form):
+    # in bitmap steps a frontier vertex marked again earlier in its own step
+    # is expanded in the next step only: the fixpoint (distances,
+    # lowest-index parents) is the same with and without the skip; queue
+    # steps never skip
+    for wl in (gg.rmat_u32(14, 16, nsrc=2, seed=51), gg.grid_f32(200, 0.01, nsrc=2, seed=52)):
+        g = graph(dawn, wl, form)
+        for s in wl.sources:
+            stats = {}
+            for skip in (0, 1):
+                g.set_option(dawn.DAWN_OPT_SKIP_REMARKED, skip)
+                exact(wl.row_ptr, wl.col, wl.weights, int(s), *solve(g, s))
+                stats[skip] = g.stats()
+            assert stats[0]["edges_skipped"] == 0
+            assert 0 <= stats[1]["edges_skipped"] <= stats[1]["edges_scanned"]
+            if form == "queue":
+                assert stats[1]["edges_skipped"] == 0
+    # signed weights and Algorithm 1 (which never skips)
+    rp, cl, w = gg.random_small(2000, 16000, 53, kind="u32", wlo=1, whi=30)
+    g = graph(dawn, (rp, cl, w), form)
+    g.set_option(dawn.DAWN_OPT_GSVM, 1)
+    exact(rp, cl, w, 0, *solve(g, 0))
+    assert g.stats()["edges_skipped"] == 0
+
+
+def test_skip_remarked_counts_on_a_random_graph(dawn):
+    # on a random graph with a wide weight range some frontier vertices are
+    # lowered again before their expansion within a step: the skip finds them
+    rp, cl = gg.erdos_renyi(1 << 16, 16 << 16, seed=54)
+    w = gg.weights_u32(len(cl), 1, 255, seed=55)
+    g = graph(dawn, (rp, cl, w), "bitmap")
+    total = 0
+    for s in (0, 1000, 40000):
+        exact(rp, cl, w, s, *solve(g, s))
+        total += g.stats()["edges_skipped"]
+    assert total > 0
