@@ -61,6 +61,7 @@ struct BlockShared {
   unsigned long long scan[kWarpsPerBlock];
   int32_t flag;
   int32_t any_mark;               // direct steps: some warp of the block made a strict improvement
+  unsigned long long trace_sum[2];  // direct steps of a traced solve: the block's frontier and edges this step
   unsigned long long bar_target;  // arrivals that end the next device-wide barrier (thread 0)
   WarpTile wt[kWarpsPerBlock];
 };
@@ -693,6 +694,7 @@ __global__ void __launch_bounds__(kBlockThreads, MINB) govm_kernel(GovmParams p)
   if (tid == 0) {
     sh.bar_target = 0;
     sh.any_mark = 0;
+    sh.trace_sum[0] = sh.trace_sum[1] = 0;
   }
   for (int s = lane; s < kTile; s += 32) sh.wt[warp].own[s] = 0;
   __syncwarp();
@@ -776,13 +778,18 @@ __global__ void __launch_bounds__(kBlockThreads, MINB) govm_kernel(GovmParams p)
           df += __shfl_down_sync(kFull, df, d);
           de += __shfl_down_sync(kFull, de, d);
         }
-        if (lane == 0 && df) atomicAdd(&ctl->frontier_sum, df);
-        if (lane == 0 && de) atomicAdd(&ctl->edges_scanned, de);
+        if (lane == 0 && df) atomicAdd(&sh.trace_sum[0], df);
+        if (lane == 0 && de) atomicAdd(&sh.trace_sum[1], de);
       }
       __syncthreads();
       if (tid == 0 && sh.any_mark) {  // one flag write per block; the barrier's release publishes it
         atomicOr(&ctl->marks[step % 3], 1u);
         sh.any_mark = 0;
+      }
+      if (tid == 0 && p.trace) {  // one counter update per block
+        if (sh.trace_sum[0]) atomicAdd(&ctl->frontier_sum, sh.trace_sum[0]);
+        if (sh.trace_sum[1]) atomicAdd(&ctl->edges_scanned, sh.trace_sum[1]);
+        sh.trace_sum[0] = sh.trace_sum[1] = 0;
       }
       if (!grid_barrier(ctl, p.wait_limit_ns, &sh.flag, &sh.bar_target)) break;
     }
