@@ -248,6 +248,10 @@ int dawn_get_stats(dawn_graph g, dawn_stats *out);
  *                          persistent kernel; DAWN_SMALL_WHEN_STATE_FITS:
  *                          the small kernel whenever the state fits (the CSR
  *                          is then read from global memory).  Same results.
+ *                          A call that wants no parents on a graph of
+ *                          non-negative weights with at most 65,536 vertices
+ *                          keeps only 32-bit distances there (half the
+ *                          shared memory; two instances per SM).
  *   DAWN_OPT_TEST_FAIL_ALLOC  N > 0: the N-th next allocation of this
  *                          handle's workspace (solver, backward scratch,
  *                          trace) fails with DAWN_ERR_OOM without touching

@@ -349,16 +349,21 @@ uint32_t weight_limit(int wtype) {
   return 0;
 }
 
-// One persistent launch.  `accumulate` (later launches of one batched call)
-// keeps the status and the counters of the earlier launches: only the
-// barrier word and the per-step change flags start again from zero.
+// The small-graph kernel's compact form (32-bit keys, 16-bit frontier ids)
+// serves calls that want no parents on graphs of non-negative weights with
+// at most 65,536 vertices.
+bool small_compact(dawn_graph g, bool parents) {
+  return !parents && g->wtype != DAWN_W_I32 && g->n <= 65536;
+}
+
 // The small-graph kernel's mode for this handle and call: 0 = not used,
 // 1 = with the solver state in shared memory, 2 = with the CSR there too.
-int small_mode(dawn_graph g) {
+int small_mode(dawn_graph g, bool compact) {
   if (g->small_path == DAWN_SMALL_NEVER || g->gsvm || g->test_stall || g->trace) return 0;
   const size_t limit = dawn::small_smem_limit();
-  if (dawn::small_layout(g->n, g->m, true).total <= limit) return 2;
-  if (g->small_path == DAWN_SMALL_WHEN_STATE_FITS && dawn::small_layout(g->n, g->m, false).total <= limit) return 1;
+  if (dawn::small_layout(g->n, g->m, true, compact).total <= limit) return 2;
+  if (g->small_path == DAWN_SMALL_WHEN_STATE_FITS && dawn::small_layout(g->n, g->m, false, compact).total <= limit)
+    return 1;
   return 0;
 }
 
@@ -370,9 +375,13 @@ int direct_steps(dawn_graph g, int32_t k) {
   return g->frontier == DAWN_FRONTIER_BITMAP || g->max_deg <= dawn::kDirectMaxDegree;
 }
 
+// One persistent launch.  `accumulate` (later launches of one batched call)
+// keeps the status and the counters of the earlier launches: only the
+// barrier word and the per-step change flags start again from zero.
 int run_solve(dawn_graph g, const int32_t *seeds, int32_t nseeds, int32_t source, int32_t k, int roots_mode,
               void *dist, int32_t *parent, int32_t *parent_edge, cudaStream_t stream, bool accumulate = false) {
-  const int small = small_mode(g);
+  const bool compact = small_compact(g, parent || parent_edge);
+  const int small = small_mode(g, compact);
   int rc = small ? DAWN_OK : ensure_workspace(g, k);  // the small kernel keeps its state on-chip
   if (rc) return rc;
   GovmParams p = {};
@@ -418,7 +427,7 @@ int run_solve(dawn_graph g, const int32_t *seeds, int32_t nseeds, int32_t source
   if (e == cudaSuccess && g->trace)
     e = cudaMemsetAsync(g->trace, 0, (size_t)g->trace_cap * 4 * sizeof(unsigned long long), stream);
   if (e != cudaSuccess) return cuda_fail(e);
-  e = small ? dawn::launch_govm_small(p, g->wtype, roots_mode ? 1 : k, small == 2, stream)
+  e = small ? dawn::launch_govm_small(p, g->wtype, roots_mode ? 1 : k, small == 2, compact, stream)
             : dawn::launch_govm(p, g->wtype, kernel_ctas(g), grid_for(g, k), stream);
   if (e != cudaSuccess) return cuda_fail(e);
   g->last_stream = stream;
@@ -488,7 +497,9 @@ int launch_limits(dawn_graph g, LaunchLimits *out) {
   out->grid_blocks = g->grid_blocks;
   out->batch = g->batch;
   out->small_path = g->small_path;
-  out->small_state_fits = dawn::small_layout(g->n, g->m, false).total <= dawn::small_smem_limit();
+  // the tuner times its candidates without parent outputs
+  out->small_state_fits =
+      dawn::small_layout(g->n, g->m, false, small_compact(g, false)).total <= dawn::small_smem_limit();
   return DAWN_OK;
 }
 }  // namespace dawn

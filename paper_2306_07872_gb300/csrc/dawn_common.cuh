@@ -117,9 +117,12 @@ constexpr int kSmallWarps = kSmallThreads / 32;
 struct SmallLayout {  // byte offsets in the block's dynamic shared memory
   size_t state, bitmap, front, scan, row_ptr, cw, total;
 };
-__host__ __device__ SmallLayout small_layout(int32_t n, int64_t m, bool csr);
+// compact: 32-bit keys and 16-bit frontier ids (no parents, weights >= 0,
+// n <= 65,536), half the shared memory of the packed form.
+__host__ __device__ SmallLayout small_layout(int32_t n, int64_t m, bool csr, bool compact);
 size_t small_smem_limit();  // the device's opt-in shared memory per block
-cudaError_t launch_govm_small(const GovmParams &p, int wtype, int32_t blocks, bool csr_in_smem, cudaStream_t stream);
+cudaError_t launch_govm_small(const GovmParams &p, int wtype, int32_t blocks, bool csr_in_smem, bool compact,
+                              cudaStream_t stream);
 
 // Launch limits and current launch options of a handle (dawn_api.cu), for
 // the autotuner (dawn_tune.cu), which otherwise uses only the public API.

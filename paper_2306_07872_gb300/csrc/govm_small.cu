@@ -17,9 +17,17 @@
 //          block-wide prefix sum and cleared.
 // The same (distance, lowest parent edge) fixpoint as the persistent kernel
 // results: both are exact minima of the packed keys.
+// Compact form, for solves that want no parents on graphs with non-negative
+// weights and at most 65,536 vertices: alpha holds the 32-bit distance keys
+// alone and delta 16-bit vertex ids, half the shared memory, so that two
+// instances fit on an SM (each block's barrier waits overlap the other's
+// work).  The distances are the same minima; with non-negative weights no
+// candidate can beat a source's zero key, so the source guard needs no parent
+// field to tell a source apart.
 #include <cuda_runtime.h>
 
 #include <atomic>
+#include <type_traits>
 
 #include "dawn_common.cuh"
 #include "dawn_keys.cuh"
@@ -28,12 +36,12 @@ namespace dawn {
 
 __host__ __device__ static inline size_t round16(size_t x) { return (x + 15) & ~(size_t)15; }
 
-__host__ __device__ SmallLayout small_layout(int32_t n, int64_t m, bool csr) {
+__host__ __device__ SmallLayout small_layout(int32_t n, int64_t m, bool csr, bool compact) {
   SmallLayout L{};
   L.state = 0;
-  L.bitmap = L.state + round16(8 * (size_t)n);
+  L.bitmap = L.state + round16((compact ? 4 : 8) * (size_t)n);
   L.front = L.bitmap + round16(4 * (size_t)((n + 31) / 32));
-  L.scan = L.front + round16(4 * (size_t)n);
+  L.scan = L.front + round16((compact ? 2 : 4) * (size_t)n);
   L.row_ptr = L.scan + round16(4 * (size_t)(2 * kSmallWarps + 2));
   L.cw = L.row_ptr + (csr ? round16(4 * ((size_t)n + 1)) : 0);
   L.total = L.cw + (csr ? round16(8 * (size_t)m) : 0);
@@ -79,7 +87,8 @@ __device__ __forceinline__ int32_t block_prefix(int32_t x, int32_t *sc, int32_t 
 // marked vertices to *marks (thread-local partial sums).  Each thread owns a
 // contiguous range of vertices, so all threads share the work however few
 // bitmap words there are.
-__device__ int32_t small_build(int32_t n, const int32_t *rp, uint32_t *bm, int32_t *front, int32_t *sc,
+template <typename FrontT>
+__device__ int32_t small_build(int32_t n, const int32_t *rp, uint32_t *bm, FrontT *front, int32_t *sc,
                                unsigned long long *edges, unsigned long long *marks) {
   const int32_t per = (n + (int32_t)blockDim.x - 1) / (int32_t)blockDim.x;
   const int32_t v0 = (int32_t)threadIdx.x * per, v1 = min(v0 + per, n);
@@ -96,21 +105,23 @@ __device__ int32_t small_build(int32_t n, const int32_t *rp, uint32_t *bm, int32
   int32_t total = 0;
   int32_t at = block_prefix(mine, sc, &total);
   for (int32_t v = v0; v < v1; ++v)
-    if ((bm[v >> 5] & (1u << (v & 31))) && rp[v + 1] > rp[v]) front[at++] = v;
+    if ((bm[v >> 5] & (1u << (v & 31))) && rp[v + 1] > rp[v]) front[at++] = (FrontT)v;
   __syncthreads();  // every thread has read beta
   for (int32_t w = threadIdx.x; w < (n + 31) / 32; w += blockDim.x) bm[w] = 0u;
   __syncthreads();
   return total;
 }
 
-template <int WT>
-__global__ void __launch_bounds__(kSmallThreads) govm_small_kernel(GovmParams p, int32_t csr_in_smem,
-                                                                   int32_t group) {
+template <int WT, bool COMPACT>
+__global__ void __launch_bounds__(kSmallThreads, COMPACT ? 2 : 1) govm_small_kernel(GovmParams p, int32_t csr_in_smem,
+                                                                                   int32_t group) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const SmallLayout L = small_layout(p.n, p.m, csr_in_smem != 0);
-  unsigned long long *st = reinterpret_cast<unsigned long long *>(smem + L.state);
+  using FrontT = typename std::conditional<COMPACT, uint16_t, int32_t>::type;
+  const SmallLayout L = small_layout(p.n, p.m, csr_in_smem != 0, COMPACT);
+  unsigned long long *st = reinterpret_cast<unsigned long long *>(smem + L.state);  // packed form
+  uint32_t *sk = reinterpret_cast<uint32_t *>(smem + L.state);                      // compact form: keys
   uint32_t *bm = reinterpret_cast<uint32_t *>(smem + L.bitmap);
-  int32_t *front = reinterpret_cast<int32_t *>(smem + L.front);
+  FrontT *front = reinterpret_cast<FrontT *>(smem + L.front);
   int32_t *sc = reinterpret_cast<int32_t *>(smem + L.scan);
   const int tid = threadIdx.x, lane = tid & 31;
   const int32_t n = p.n, inst = blockIdx.x;
@@ -129,7 +140,10 @@ __global__ void __launch_bounds__(kSmallThreads) govm_small_kernel(GovmParams p,
   }
 
   // 1. alpha = +inf, beta = {}; the CSR into shared memory when it fits.
-  for (int32_t v = tid; v < n; v += blockDim.x) st[v] = kInfState;
+  for (int32_t v = tid; v < n; v += blockDim.x) {
+    if (COMPACT) sk[v] = Key<WT>::inf;
+    else st[v] = kInfState;
+  }
   for (int32_t w = tid; w < (n + 31) / 32; w += blockDim.x) bm[w] = 0u;
   const int32_t *rp = p.row_ptr;
   const uint2 *cw = p.cw;
@@ -151,7 +165,8 @@ __global__ void __launch_bounds__(kSmallThreads) govm_small_kernel(GovmParams p,
       atomicCAS(&ctl->status, 0, (int)DAWN_ERR_INVALID);
       continue;
     }
-    st[s] = kSourceState;
+    if (COMPACT) sk[s] = Key<WT>::zero;
+    else st[s] = kSourceState;
     atomicOr(bm + (s >> 5), 1u << (s & 31));
   }
   __syncthreads();
@@ -171,17 +186,25 @@ __global__ void __launch_bounds__(kSmallThreads) govm_small_kernel(GovmParams p,
     esum += edges_cur;
     for (int32_t fi = gid; fi < count; fi += ngroups) {
       const int32_t u = front[fi];
-      const uint32_t du = (uint32_t)(st[u] >> 32);  // alpha[u] in place, as Algorithm 2 reads it
+      // alpha[u] in place, as Algorithm 2 reads it
+      const uint32_t du = COMPACT ? sk[u] : (uint32_t)(st[u] >> 32);
       const int32_t b = rp[u], e = rp[u + 1];
       for (int32_t x = b + glane; x < e; x += group) {
         const uint2 c = cw[x];
         const uint32_t t = c.x;
         const uint32_t ckey = Key<WT>::add(du, c.y);
-        const unsigned long long cand = ((unsigned long long)ckey << 32) | (uint32_t)x;
-        const unsigned long long cur = st[t];
-        if (cand < cur && cur != kSourceState) {  // the source guard: never relax into a source
-          const unsigned long long old = atomicMin(st + t, cand);
-          if (ckey < (uint32_t)(old >> 32)) atomicOr(bm + (t >> 5), 1u << (t & 31));
+        if (COMPACT) {  // keys alone: a source's zero key is never beaten (weights >= 0)
+          if (ckey < sk[t]) {
+            const uint32_t old = atomicMin(sk + t, ckey);
+            if (ckey < old) atomicOr(bm + (t >> 5), 1u << (t & 31));
+          }
+        } else {
+          const unsigned long long cand = ((unsigned long long)ckey << 32) | (uint32_t)x;
+          const unsigned long long cur = st[t];
+          if (cand < cur && cur != kSourceState) {  // the source guard: never relax into a source
+            const unsigned long long old = atomicMin(st + t, cand);
+            if (ckey < (uint32_t)(old >> 32)) atomicOr(bm + (t >> 5), 1u << (t & 31));
+          }
         }
       }
     }
@@ -195,6 +218,10 @@ __global__ void __launch_bounds__(kSmallThreads) govm_small_kernel(GovmParams p,
   int32_t *par = p.parent ? p.parent + (size_t)inst * n : nullptr;
   int32_t *pe = p.parent_edge ? p.parent_edge + (size_t)inst * n : nullptr;
   for (int32_t v = tid; v < n; v += blockDim.x) {
+    if (COMPACT) {  // no parent output in this form
+      dist[v] = Key<WT>::out(sk[v]);
+      continue;
+    }
     const unsigned long long s = st[v];
     const uint32_t key = (uint32_t)(s >> 32), e = (uint32_t)s;
     const bool unreachable = key == Key<WT>::inf;
@@ -216,10 +243,11 @@ __global__ void __launch_bounds__(kSmallThreads) govm_small_kernel(GovmParams p,
 
 using SmallFn = void (*)(GovmParams, int32_t, int32_t);
 
-SmallFn small_for(int wtype) {
-  if (wtype == DAWN_W_F32) return govm_small_kernel<DAWN_W_F32>;
-  if (wtype == DAWN_W_I32) return govm_small_kernel<DAWN_W_I32>;
-  return govm_small_kernel<DAWN_W_U32>;
+// The compact form exists for the non-negative weight types only.
+SmallFn small_for(int wtype, bool compact) {
+  if (wtype == DAWN_W_F32) return compact ? govm_small_kernel<DAWN_W_F32, true> : govm_small_kernel<DAWN_W_F32, false>;
+  if (wtype == DAWN_W_I32) return govm_small_kernel<DAWN_W_I32, false>;
+  return compact ? govm_small_kernel<DAWN_W_U32, true> : govm_small_kernel<DAWN_W_U32, false>;
 }
 
 }  // namespace
@@ -232,7 +260,8 @@ size_t small_smem_limit() {
   return (size_t)v;
 }
 
-cudaError_t launch_govm_small(const GovmParams &p, int wtype, int32_t blocks, bool csr_in_smem, cudaStream_t stream) {
+cudaError_t launch_govm_small(const GovmParams &p, int wtype, int32_t blocks, bool csr_in_smem, bool compact,
+                              cudaStream_t stream) {
   static std::atomic<unsigned long long> done{0};  // kernels opted in to the large shared memory, per device
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -241,15 +270,22 @@ cudaError_t launch_govm_small(const GovmParams &p, int wtype, int32_t blocks, bo
   const size_t limit = small_smem_limit();
   if (!(done.load() & bit)) {
     for (int w : {DAWN_W_U32, DAWN_W_F32, DAWN_W_I32})
-      if (e == cudaSuccess) e = cudaFuncSetAttribute(small_for(w), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit);
+      for (bool c : {false, true}) {
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(small_for(w, c), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)limit);
+        // the compact form wants two blocks' worth of shared memory per SM
+        if (e == cudaSuccess && c)
+          e = cudaFuncSetAttribute(small_for(w, c), cudaFuncAttributePreferredSharedMemoryCarveout,
+                                   (int)cudaSharedmemCarveoutMaxShared);
+      }
     if (e != cudaSuccess) return e;
     done.fetch_or(bit);
   }
-  const size_t bytes = small_layout(p.n, p.m, csr_in_smem).total;
+  compact = compact && wtype != DAWN_W_I32 && p.n <= 65536 && !p.parent && !p.parent_edge;
+  const size_t bytes = small_layout(p.n, p.m, csr_in_smem, compact).total;
   // threads per frontier vertex: the average out-degree rounded up to a power of two, 2..32
   int32_t group = 2;
   while (group < 32 && (int64_t)group * p.n < p.m) group <<= 1;
-  small_for(wtype)<<<(unsigned)blocks, kSmallThreads, bytes, stream>>>(p, csr_in_smem ? 1 : 0, group);
+  small_for(wtype, compact)<<<(unsigned)blocks, kSmallThreads, bytes, stream>>>(p, csr_in_smem ? 1 : 0, group);
   return cudaGetLastError();
 }
 

@@ -129,3 +129,33 @@ def test_small_kernel_edge_cases_and_errors(dawn):
     dist = torch.full((g.n,), 9, dtype=torch.float32, device="cuda")
     dawn.dawn_sssp(g.handle, 0, dist)
     assert dawn.dawn_status(g.handle) == dawn.DAWN_ERR_INVALID and bool((dist == 9).all())
+
+
+@pytest.mark.parametrize("name", [c[0] for c in CASES])
+@pytest.mark.parametrize("mode", ["auto", "state"])
+def test_small_kernel_compact_form_without_parents(dawn, name, mode):
+    # solves that want no parents on graphs of non-negative weights run the
+    # compact form (32-bit keys, 16-bit frontier ids, two blocks per SM):
+    # the same distances as the oracle; signed weights keep the packed form
+    rp, cl, w, s = dict(CASES)[name]()
+    g = dawn.Graph(rp, cl, w)
+    g.set_option(dawn.DAWN_OPT_SMALL_PATH, dawn.DAWN_SMALL_AUTO if mode == "auto" else dawn.DAWN_SMALL_WHEN_STATE_FITS)
+    d_ref = oracle.sssp(rp, cl, w, s)[0]
+    d, _, _ = g.sssp(int(s), parent=False)
+    assert np.array_equal(bits(d.cpu().numpy()), bits(d_ref))
+    srcs = np.array([s, 0, len(rp) - 2, s], np.int32)
+    D, _ = g.msssp(srcs, parent=False)
+    D = D.cpu().numpy()
+    for i, r in enumerate(srcs):
+        assert np.array_equal(bits(D[i]), bits(oracle.sssp(rp, cl, w, int(r))[0])), i
+    dr, _, _ = g.sssp_roots(srcs[:3], parent=False)
+    assert np.array_equal(bits(dr.cpu().numpy()), bits(oracle.sssp(rp, cl, w, srcs[:3])[0]))
+
+
+def test_small_kernel_compact_apsp_against_floyd_warshall(dawn):
+    # every vertex a source, no parents: the compact form, checked against
+    # all-pairs Floyd-Warshall (exact for integer weights)
+    wl = gg.tiny_er(n=512, avg_deg=6, seed=46)
+    g = dawn.Graph(wl.row_ptr, wl.col, wl.weights)
+    D, _ = g.msssp(np.arange(wl.n, dtype=np.int32), parent=False)
+    assert np.array_equal(D.cpu().numpy(), oracle.floyd_warshall(wl.row_ptr, wl.col, wl.weights))
