@@ -446,6 +446,7 @@ def run_e2e(args, wl, device, world, tuning=None):
         if tuning:
             dawn.dawn_set_option(h, dawn.DAWN_OPT_CTAS_PER_SM, tuning["ctas_per_sm"])
             dawn.dawn_set_option(h, dawn.DAWN_OPT_GRID_BLOCKS, tuning["grid_blocks"])
+            dawn.dawn_set_option(h, dawn.DAWN_OPT_FRONTIER, tuning["frontier"])
         return h
 
     def solve(h):
@@ -575,6 +576,7 @@ def leg_msssp(args, device=0):
             dawn.dawn_set_option(g.handle, dawn.DAWN_OPT_GRID_BLOCKS, t["grid_blocks"])
             dawn.dawn_set_option(g.handle, dawn.DAWN_OPT_BATCH, t["batch"])
             dawn.dawn_set_option(g.handle, dawn.DAWN_OPT_SMALL_PATH, t["small_path"])
+            dawn.dawn_set_option(g.handle, dawn.DAWN_OPT_FRONTIER, t["frontier"])
     with Clocks(device) as clk:
         use(tune_batch)
         tb = timed_calls(lambda: dawn.dawn_msssp(g.handle, src, dist, par), 5, flush=flush)

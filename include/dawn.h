@@ -322,8 +322,10 @@ int dawn_set_option(dawn_graph g, int option, int64_t value);
  * two builds of the persistent kernel (4 or 5 CTAs per SM) times the grid
  * sizes {all co-resident CTAs, 3/4, 1/2, 1/4 of them, one per SM, the
  * automatic size}, times, in DAWN_TUNE_MSSSP mode, the batch sizes {largest,
- * 1/2, 1/4 of it}, and the small-graph kernel when the graph's solver state
- * fits in shared memory (DAWN_OPT_SMALL_PATH).  Results do not depend on
+ * 1/2, 1/4 of it}; in the single-instance modes, the step form that
+ * DAWN_FRONTIER_AUTO does not pick (queue or bitmap steps, DAWN_OPT_FRONTIER)
+ * with each build at the automatic grid size; and the small-graph kernel
+ * when the graph's solver state fits in shared memory (DAWN_OPT_SMALL_PATH).  Results do not depend on
  * the configuration (the solver's fixpoint is order-independent); only the
  * time does.
  *   mode     DAWN_TUNE_SSSP: dawn_sssp from each source in turn;
@@ -347,6 +349,7 @@ typedef struct {
   float best_ms;        /* median workload time with the chosen configuration */
   float default_ms;     /* median workload time with the default options */
   int32_t small_path;   /* chosen DAWN_OPT_SMALL_PATH */
+  int32_t frontier;     /* chosen DAWN_OPT_FRONTIER (DAWN_FRONTIER_AUTO unless the other step form won) */
 } dawn_tuning;
 
 enum { DAWN_TUNE_SSSP = 0, DAWN_TUNE_MSSSP = 1, DAWN_TUNE_ROOTS = 2 };

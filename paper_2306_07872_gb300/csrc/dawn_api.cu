@@ -497,6 +497,8 @@ int launch_limits(dawn_graph g, LaunchLimits *out) {
   out->grid_blocks = g->grid_blocks;
   out->batch = g->batch;
   out->small_path = g->small_path;
+  out->frontier = g->frontier;
+  out->auto_frontier = g->max_deg <= dawn::kDirectMaxDegree ? DAWN_FRONTIER_BITMAP : DAWN_FRONTIER_QUEUE;
   // the tuner times its candidates without parent outputs
   out->small_state_fits =
       dawn::small_layout(g->n, g->m, false, small_compact(g, false)).total <= dawn::small_smem_limit();

@@ -136,6 +136,8 @@ struct LaunchLimits {
   int batch;            // current DAWN_OPT_BATCH
   int small_path;       // current DAWN_OPT_SMALL_PATH
   int small_state_fits;  // the small-graph kernel could hold this graph's solver state
+  int frontier;         // current DAWN_OPT_FRONTIER
+  int auto_frontier;    // the form DAWN_FRONTIER_AUTO gives a single-instance solve (queue or bitmap)
 };
 int launch_limits(dawn_graph g, LaunchLimits *out);
 

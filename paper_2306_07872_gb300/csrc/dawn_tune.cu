@@ -1,6 +1,7 @@
 // Launch autotuner: picks the kernel (persistent or small-graph), the
-// persistent kernel's build (CTAs per SM) and grid size, and the msssp batch
-// size for one graph and workload by timing candidates with CUDA events.  The paper has no counterpart (its launch
+// persistent kernel's build (CTAs per SM), grid size and frontier form
+// (queue or bitmap steps), and the msssp batch size for one graph and
+// workload by timing candidates with CUDA events.  The paper has no counterpart (its launch
 // shape is fixed); every solve it times runs through the public API, so a
 // tuned configuration is exactly what later solves on the handle use.
 #include <cuda_runtime.h>
@@ -13,16 +14,17 @@
 namespace {
 
 struct Candidate {
-  int ctas;   // DAWN_OPT_CTAS_PER_SM
-  int grid;   // DAWN_OPT_GRID_BLOCKS (0 = automatic)
-  int batch;  // DAWN_OPT_BATCH (0 = automatic)
-  int small;  // DAWN_OPT_SMALL_PATH
+  int ctas;      // DAWN_OPT_CTAS_PER_SM
+  int grid;      // DAWN_OPT_GRID_BLOCKS (0 = automatic)
+  int batch;     // DAWN_OPT_BATCH (0 = automatic)
+  int small;     // DAWN_OPT_SMALL_PATH
+  int frontier;  // DAWN_OPT_FRONTIER
 };
 
 // Restores a handle's launch options unless released.
 struct OptionGuard {
   dawn_graph g;
-  int ctas, grid, batch, small;
+  int ctas, grid, batch, small, frontier;
   bool armed = true;
   ~OptionGuard() {
     if (!armed) return;
@@ -30,6 +32,7 @@ struct OptionGuard {
     dawn_set_option(g, DAWN_OPT_GRID_BLOCKS, grid);
     dawn_set_option(g, DAWN_OPT_BATCH, batch);
     dawn_set_option(g, DAWN_OPT_SMALL_PATH, small);
+    dawn_set_option(g, DAWN_OPT_FRONTIER, frontier);
   }
 };
 
@@ -50,6 +53,7 @@ int apply(dawn_graph g, const Candidate &c) {
   if (!rc) rc = dawn_set_option(g, DAWN_OPT_GRID_BLOCKS, c.grid);
   if (!rc) rc = dawn_set_option(g, DAWN_OPT_BATCH, c.batch);
   if (!rc) rc = dawn_set_option(g, DAWN_OPT_SMALL_PATH, c.small);
+  if (!rc) rc = dawn_set_option(g, DAWN_OPT_FRONTIER, c.frontier);
   return rc;
 }
 
@@ -122,17 +126,22 @@ extern "C" int dawn_autotune(dawn_graph g, int mode, const int32_t *sources, int
   // The default configuration comes first, so it wins ties; it may run the
   // small-graph kernel, the shapes after it the persistent one, and the
   // small kernel is tried on its own when the solver state fits on-chip.
-  std::vector<Candidate> cands = {{5, 0, 0, DAWN_SMALL_AUTO}};
+  std::vector<Candidate> cands = {{5, 0, 0, DAWN_SMALL_AUTO, DAWN_FRONTIER_AUTO}};
   const std::vector<int> batches =
       mode == DAWN_TUNE_MSSSP ? batch_candidates(kk, lim.max_batch) : std::vector<int>{0};
   for (int ctas : {5, 4}) {
     const int cap = (ctas == 4 ? lim.occupancy4 : lim.occupancy5) * lim.sms;
     for (int grid : grid_candidates(cap, lim.sms))
-      for (int batch : batches) cands.push_back({ctas, grid, batch, DAWN_SMALL_NEVER});
+      for (int batch : batches) cands.push_back({ctas, grid, batch, DAWN_SMALL_NEVER, DAWN_FRONTIER_AUTO});
+    // single-instance solves may run either step form: the one the automatic
+    // rule does not pick is timed at the automatic grid size
+    if (mode != DAWN_TUNE_MSSSP)
+      for (int form : {DAWN_FRONTIER_QUEUE, DAWN_FRONTIER_BITMAP})
+        if (form != lim.auto_frontier) cands.push_back({ctas, 0, 0, DAWN_SMALL_NEVER, form});
   }
-  if (lim.small_state_fits) cands.push_back({5, 0, 0, DAWN_SMALL_WHEN_STATE_FITS});
+  if (lim.small_state_fits) cands.push_back({5, 0, 0, DAWN_SMALL_WHEN_STATE_FITS, DAWN_FRONTIER_AUTO});
 
-  OptionGuard guard{g, lim.ctas_per_sm, lim.grid_blocks, lim.batch, lim.small_path};
+  OptionGuard guard{g, lim.ctas_per_sm, lim.grid_blocks, lim.batch, lim.small_path, lim.frontier};
   float best_ms = 0.0f, default_ms = 0.0f;
   size_t best = 0;
   std::vector<float> t(reps);
@@ -163,6 +172,7 @@ extern "C" int dawn_autotune(dawn_graph g, int mode, const int32_t *sources, int
     out->grid_blocks = b.grid;
     out->batch = b.batch;
     out->small_path = b.small;
+    out->frontier = b.frontier;
     out->candidates = (int32_t)cands.size();
     out->best_ms = best_ms;
     out->default_ms = default_ms;

@@ -54,7 +54,7 @@ class _Stats(ctypes.Structure):
 class _Tuning(ctypes.Structure):
     _fields_ = [("ctas_per_sm", ctypes.c_int32), ("grid_blocks", ctypes.c_int32), ("batch", ctypes.c_int32),
                 ("candidates", ctypes.c_int32), ("best_ms", ctypes.c_float), ("default_ms", ctypes.c_float),
-                ("small_path", ctypes.c_int32)]
+                ("small_path", ctypes.c_int32), ("frontier", ctypes.c_int32)]
 
 
 _lib = None
@@ -350,6 +350,7 @@ class Graph:
                 self.set_option(DAWN_OPT_GRID_BLOCKS, hit["grid_blocks"])
                 self.set_option(DAWN_OPT_BATCH, hit["batch"])
                 self.set_option(DAWN_OPT_SMALL_PATH, hit.get("small_path", DAWN_SMALL_AUTO))
+                self.set_option(DAWN_OPT_FRONTIER, hit.get("frontier", DAWN_FRONTIER_AUTO))
                 return dict(hit, cached=True)
         with torch.cuda.device(self.device):
             res = dawn_autotune(self.handle, m, sources, reps, stream)
@@ -382,8 +383,8 @@ def tune_cache_store(path: str, key: str, result: dict):
     """Adds one entry; the file is replaced atomically."""
     import json
     data = tune_cache_load(path)
-    data[key] = {f: result[f] for f in ("ctas_per_sm", "grid_blocks", "batch", "small_path", "best_ms", "default_ms")
-                 if f in result}
+    data[key] = {f: result[f] for f in ("ctas_per_sm", "grid_blocks", "batch", "small_path", "frontier", "best_ms",
+                                        "default_ms") if f in result}
     tmp = f"{path}.tmp{os.getpid()}"
     with open(tmp, "w") as f:
         json.dump(data, f, indent=1, sort_keys=True)

@@ -85,11 +85,13 @@ def test_tune_cache_keys_and_store(tmp_path):
     assert k1 != d.tune_cache_key(4194304, 65243778, 0, "sssp", 8, "B200/148")  # GPU model
     path = str(tmp_path / "tune.json")
     assert d.tune_cache_load(path) == {}
-    res = {"ctas_per_sm": 4, "grid_blocks": 608, "batch": 0, "best_ms": 1.0, "default_ms": 1.1, "candidates": 11}
+    res = {"ctas_per_sm": 4, "grid_blocks": 608, "batch": 0, "best_ms": 1.0, "default_ms": 1.1, "candidates": 11,
+           "frontier": 2}
     d.tune_cache_store(path, k1, res)
     d.tune_cache_store(path, "other", dict(res, grid_blocks=0))
     got = d.tune_cache_load(path)
     assert got[k1]["grid_blocks"] == 608 and got["other"]["grid_blocks"] == 0 and "candidates" not in got[k1]
+    assert got[k1]["frontier"] == 2
     (tmp_path / "bad.json").write_text("not json")
     assert d.tune_cache_load(str(tmp_path / "bad.json")) == {}
 

@@ -93,10 +93,27 @@ def test_autotune_sssp_keeps_results_exact(dawn):
     t = g.autotune(wl.sources, mode="sssp", reps=2)
     assert t["ctas_per_sm"] in (4, 5)
     assert t["grid_blocks"] >= 0 and t["batch"] == 0
-    assert t["candidates"] >= 8
+    assert t["candidates"] >= 10  # the launch shapes plus the other step form at each build
     assert 0 < t["best_ms"] <= t["default_ms"]
+    assert t["frontier"] in (dawn.DAWN_FRONTIER_AUTO, dawn.DAWN_FRONTIER_QUEUE, dawn.DAWN_FRONTIER_BITMAP)
     for s in wl.sources:
         exact(g, wl.row_ptr, wl.col, wl.weights, s)
+
+
+def test_autotune_frontier_form_applies(dawn):
+    # whichever step form the tuner keeps is what later solves run, and it
+    # gives the oracle's fixpoint; on a light graph the tuner may keep queue
+    # steps only if they timed faster than the automatic bitmap steps
+    wl = gg.grid_f32(300, 0.01, nsrc=4, seed=31)
+    g = dawn.Graph(wl.row_ptr, wl.col, wl.weights)
+    g.set_option(dawn.DAWN_OPT_SMALL_PATH, dawn.DAWN_SMALL_NEVER)
+    t = g.autotune(wl.sources, mode="sssp", reps=1)
+    assert t["frontier"] in (dawn.DAWN_FRONTIER_AUTO, dawn.DAWN_FRONTIER_QUEUE)
+    for s in wl.sources:
+        exact(g, wl.row_ptr, wl.col, wl.weights, s)
+    # the msssp mode never times a step form (batched launches use queue steps)
+    t2 = g.autotune(wl.sources, mode="msssp", reps=1)
+    assert t2["frontier"] == dawn.DAWN_FRONTIER_AUTO
 
 
 def test_autotune_msssp_and_roots(dawn):
@@ -154,7 +171,7 @@ def test_autotune_cache_reuses_a_stored_configuration(dawn, tmp_path):
     h = dawn.Graph(wl.row_ptr, wl.col, wl.weights)
     again = h.autotune(wl.sources, mode="sssp", reps=1, cache=path)
     assert again["cached"] is True
-    for f in ("ctas_per_sm", "grid_blocks", "batch"):
+    for f in ("ctas_per_sm", "grid_blocks", "batch", "frontier"):
         assert again[f] == first[f]
     for s in wl.sources:
         exact(h, wl.row_ptr, wl.col, wl.weights, s)
