@@ -5,7 +5,8 @@
 //   1. alpha = +inf (packed state), beta = {} (bitmap);
 //   2. seeds: alpha[s] = 0 and s enters beta (every instance's source, or
 //      all roots);
-//   3. build delta from beta (below), then repeat GOVM steps:
+//   3. GOVM steps, in one of two forms (a template parameter):
+//      queue steps: build delta from beta, then per step
 //      relax   every warp takes 128-edge tiles of the frontier's virtual edge
 //              list (the concatenated out-edges of all frontier vertices, so
 //              work is balanced by edges, not vertices), relaxes each edge
@@ -19,6 +20,11 @@
 //              offsets together;
 //      each phase ends with a device-wide barrier (bounded wait); the loop
 //      stops when delta is empty (no path changed) or at the step cap;
+//      bitmap steps (single-instance solves on graphs of short rows): the
+//      previous step's marks are the frontier; each warp expands the marked
+//      vertices of its bitmap words directly (same edge phase) and marks a
+//      second bitmap; one barrier per step; the loop stops after a step that
+//      lowered no distance;
 //   4. unpack dist / parent / parent_edge.
 // No host round trip happens between steps.
 #include <cuda_runtime.h>
@@ -564,9 +570,13 @@ __device__ __forceinline__ void relax_tile(const GovmParams &p, WarpTile &wt, in
 // and expands them 32 at a time, one per lane: each lane reads its vertex's
 // row bounds and, in place, its distance key; the 32 rows' out-edges are laid
 // end to end and relaxed in kTile-edge tiles with the same edge phase as
-// relax_tile.  Marks go to `bn`.  Counters: `marked` (the vertices
-// consumed), `front` (those with an out-edge) and `edges` (their out-edges).
-// Returns whether this warp made any strict improvement (a mark in bn).
+// relax_tile.  Marks go to `bn`.  With p.skip_remarked, a vertex whose bit
+// in `bn` is already set (its distance dropped again earlier in this step)
+// is not expanded now: it is in the next frontier and is expanded there with
+// a key no larger.  Counters: `marked` (the vertices consumed), `front`
+// (those with an out-edge), `edges` (their out-edges) and `skipped` (the
+// out-edges of the vertices not expanded).  Returns whether this warp made
+// any strict improvement (a mark in bn).
 template <int WT>
 __device__ bool direct_step(const GovmParams &p, uint32_t *bm, uint32_t *bn, WarpTile &wt, unsigned long long &marked,
                             unsigned long long &front, unsigned long long &edges, unsigned long long &skipped) {
