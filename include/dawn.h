@@ -101,6 +101,14 @@ typedef struct {
  *   out          receives the handle
  * The library copies the arrays; the caller keeps ownership of its inputs.
  * Validation runs on the device and is synchronous (the call waits for it).
+ * Device memory: every buffer of a handle (the graph, the solver workspace,
+ * the backward scratch, staging and trace buffers) comes from a stream-ordered
+ * memory pool per device that the library owns; no call allocates with
+ * cudaMalloc or frees with cudaFree, so no allocation or free synchronises
+ * the device.
+ * Memory a handle frees stays in the pool for the next allocation and goes
+ * back to the device when the last handle on it is destroyed.  Allocations
+ * are refused (DAWN_ERR_CUDA) on a stream that is being captured.
  * Errors: DAWN_ERR_INVALID (malformed input), DAWN_ERR_OOM, DAWN_ERR_CUDA.
  */
 int dawn_create_graph(int32_t n, int64_t m, const int32_t *row_ptr, const int32_t *col_idx,
@@ -138,6 +146,9 @@ int dawn_set_weights(dawn_graph g, const void *weights, int flags, void *stream)
  * solves grow it on demand).  Call before capturing solves into a CUDA
  * graph, since growing the workspace allocates device memory.  (Solves by
  * the small-graph kernel keep their state in shared memory and use none.)
+ * The workspace is allocated in the order of the handle's last stream (the
+ * creation stream, or the stream of its last call), which the call then
+ * synchronises.
  */
 int dawn_reserve(dawn_graph g, int32_t k);
 
@@ -413,7 +424,9 @@ int dawn_sssp_noalloc(dawn_graph g, int32_t source, void *dist, int32_t *parent,
 /* Human-readable name of a status code (static string; plumbing). */
 const char *dawn_status_string(int code);
 
-/* Free the graph and its device memory.  NULL is allowed (plumbing). */
+/* Free the graph and its device memory.  Waits for the handle's last stream,
+ * then returns its buffers to the library's pool (see dawn_create_graph).
+ * NULL is allowed (plumbing). */
 void dawn_destroy(dawn_graph g);
 
 #ifdef __cplusplus

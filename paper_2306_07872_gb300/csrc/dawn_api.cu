@@ -253,36 +253,114 @@ int cuda_fail(cudaError_t e) {
   return DAWN_ERR_CUDA;
 }
 
+// Device memory of every handle comes from one stream-ordered memory pool
+// per device that the library owns (cudaMallocFromPoolAsync /
+// cudaFreeAsync).  Freed blocks stay in the pool and serve the next
+// allocation without a new mapping, and neither call synchronises the
+// device, so a serving loop that builds the next graph while the current
+// one's solves run, then destroys the old handle, leaves no idle gap on the
+// GPU.  Reuse across streams happens only once a free has completed in its
+// stream's order (no hidden cross-stream dependencies).  When the last
+// handle on a device is destroyed, the pool is trimmed and its memory goes
+// back to the device.
+struct DevicePool {
+  cudaMemPool_t pool = nullptr;
+  int live = 0;  // handles alive on the device
+};
+constexpr int kPoolDevices = 64;
+std::mutex g_pool_mutex;
+DevicePool g_pools[kPoolDevices];
+
+cudaMemPool_t device_pool(int device) {
+  if (device < 0 || device >= kPoolDevices) return nullptr;
+  std::lock_guard<std::mutex> lock(g_pool_mutex);
+  DevicePool &d = g_pools[device];
+  if (!d.pool) {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    uint64_t keep = UINT64_MAX;  // keep freed memory for reuse until the trim
+    int off = 0;
+    if (cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess ||
+        cudaMemPoolSetAttribute(pool, cudaMemPoolReuseAllowInternalDependencies, &off) != cudaSuccess) {
+      cudaGetLastError();
+      cudaMemPoolDestroy(pool);
+      return nullptr;
+    }
+    d.pool = pool;
+  }
+  return d.pool;
+}
+
+void pool_handle_created(int device) {
+  std::lock_guard<std::mutex> lock(g_pool_mutex);
+  ++g_pools[device].live;
+}
+
+// Called after the handle's frees were enqueued and its stream synchronised.
+void pool_handle_destroyed(int device) {
+  std::lock_guard<std::mutex> lock(g_pool_mutex);
+  DevicePool &d = g_pools[device];
+  if (--d.live == 0 && d.pool) cudaMemPoolTrimTo(d.pool, 0);
+}
+
+// Stream-ordered allocation on `stream` from the device's pool: usable by
+// work on `stream` at once, and by any stream once `stream` has passed this
+// point.  Refused during stream capture (the workspace must exist before a
+// capture starts: dawn_reserve).
 template <typename T>
-int dalloc(T **p, size_t count) {
+int dalloc(int device, T **p, size_t count, cudaStream_t stream) {
   *p = nullptr;
   if (count == 0) count = 1;
-  cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
-  if (e != cudaSuccess) {
-    *p = nullptr;
-    return cuda_fail(e);
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(stream, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return DAWN_ERR_CUDA;
   }
+  cudaMemPool_t pool = device_pool(device);
+  if (!pool) return DAWN_ERR_CUDA;
+  void *q = nullptr;
+  cudaError_t e = cudaMallocFromPoolAsync(&q, count * sizeof(T), pool, stream);
+  if (e != cudaSuccess) return cuda_fail(e);
+  if ((uintptr_t)q % 16 != 0) {  // every kernel here assumes at least 16-byte alignment
+    cudaFreeAsync(q, stream);
+    return DAWN_ERR_CUDA;
+  }
+  *p = (T *)q;
   return DAWN_OK;
+}
+
+// Stream-ordered free: the block returns to the pool once `stream` reaches
+// this point, so every use of it must be ordered before that on `stream`.
+void dfree(void *p, cudaStream_t stream) {
+  if (p) cudaFreeAsync(p, stream);
 }
 
 // Allocation of a handle's workspace (solver, backward, trace), with the
 // DAWN_OPT_TEST_FAIL_ALLOC hook: a host-side stand-in for an out-of-memory
 // device, so the OOM paths are tested without exhausting a shared GPU.
 template <typename T>
-int halloc(dawn_graph g, T **p, size_t count) {
+int halloc(dawn_graph g, T **p, size_t count, cudaStream_t stream) {
   if (g->fail_alloc > 0 && --g->fail_alloc == 0) {
     *p = nullptr;
     return DAWN_ERR_OOM;
   }
-  return dalloc(p, count);
+  return dalloc(g->device, p, count, stream);
 }
 
-void free_workspace(dawn_graph g) {
-  cudaFree(g->state);
-  cudaFree(g->bitmap);
-  cudaFree(g->queue);
-  cudaFree(g->tiles);
-  cudaFree(g->tails);
+void free_workspace(dawn_graph g, cudaStream_t stream) {
+  dfree(g->state, stream);
+  dfree(g->bitmap, stream);
+  dfree(g->queue, stream);
+  dfree(g->tiles, stream);
+  dfree(g->tails, stream);
   g->state = nullptr;
   g->bitmap = nullptr;
   g->queue = nullptr;
@@ -304,17 +382,22 @@ int32_t max_chunk(dawn_graph g) {
   return (int32_t)std::max<int64_t>(1, std::min<int64_t>({(int64_t)dawn::kMaxInstancesPerLaunch, by_tiles, by_mem}));
 }
 
-int ensure_workspace(dawn_graph g, int32_t k) {
+// Grows the solver workspace to k instances, allocating on `stream`.  The
+// old workspace is freed on `stream` after the handle's previous stream has
+// drained (one stream at a time per handle, but possibly a different one).
+int ensure_workspace(dawn_graph g, int32_t k, cudaStream_t stream) {
   if (g->ws_k >= k) return DAWN_OK;
-  free_workspace(g);
+  if (g->ws_k > 0 && g->last_stream != stream && cudaStreamSynchronize(g->last_stream) != cudaSuccess)
+    return DAWN_ERR_CUDA;
+  free_workspace(g, stream);
   g->words = (g->n + 31) / 32;
   g->tiles_cap = g->m / dawn::kTile + 2;
   const size_t kn = (size_t)k * g->n;
   int rc;
-  if ((rc = halloc(g, &g->state, kn)) || (rc = halloc(g, &g->bitmap, (size_t)2 * k * g->words)) ||
-      (rc = halloc(g, &g->queue, kn)) || (rc = halloc(g, &g->tiles, (size_t)k * g->tiles_cap)) ||
-      (rc = halloc(g, &g->tails, (size_t)2 * k))) {
-    free_workspace(g);
+  if ((rc = halloc(g, &g->state, kn, stream)) || (rc = halloc(g, &g->bitmap, (size_t)2 * k * g->words, stream)) ||
+      (rc = halloc(g, &g->queue, kn, stream)) || (rc = halloc(g, &g->tiles, (size_t)k * g->tiles_cap, stream)) ||
+      (rc = halloc(g, &g->tails, (size_t)2 * k, stream))) {
+    free_workspace(g, stream);
     return rc;
   }
   g->ws_k = k;
@@ -382,7 +465,7 @@ int run_solve(dawn_graph g, const int32_t *seeds, int32_t nseeds, int32_t source
               void *dist, int32_t *parent, int32_t *parent_edge, cudaStream_t stream, bool accumulate = false) {
   const bool compact = small_compact(g, parent || parent_edge);
   const int small = small_mode(g, compact);
-  int rc = small ? DAWN_OK : ensure_workspace(g, k);  // the small kernel keeps its state on-chip
+  int rc = small ? DAWN_OK : ensure_workspace(g, k, stream);  // the small kernel keeps its state on-chip
   if (rc) return rc;
   GovmParams p = {};
   p.row_ptr = g->row_ptr;
@@ -469,18 +552,25 @@ int validate(dawn_graph g, cudaStream_t stream, bool wait = true) {
   return DAWN_OK;
 }
 
-void release(dawn_graph g) {
-  free_workspace(g);
-  cudaFree(g->row_ptr);
-  cudaFree(g->col);
-  cudaFree(g->w);
-  cudaFree(g->cw);
-  cudaFree(g->trace);
-  cudaFree(g->src);
-  cudaFree(g->ctl);
-  cudaFree(g->vflags);
-  cudaFree(g->bw_base);
+// Frees every device buffer of the handle on `stream` (which the handle's
+// work has been ordered on or has finished) and deletes it.
+void release(dawn_graph g, cudaStream_t stream, bool counted) {
+  free_workspace(g, stream);
+  dfree(g->row_ptr, stream);
+  dfree(g->col, stream);
+  dfree(g->w, stream);
+  dfree(g->cw, stream);
+  dfree(g->trace, stream);
+  dfree(g->src, stream);
+  dfree(g->ctl, stream);
+  dfree(g->vflags, stream);
+  dfree(g->bw_base, stream);
+  const int device = g->device;
   delete g;
+  if (counted) {
+    cudaStreamSynchronize(stream);  // the frees have completed: the trim can return them
+    pool_handle_destroyed(device);
+  }
 }
 
 }  // namespace
@@ -540,17 +630,24 @@ int dawn_create_graph(int32_t n, int64_t m, const int32_t *row_ptr, const int32_
     delete g;
     return DAWN_ERR_CUDA;
   }
-  if ((rc = dalloc(&g->row_ptr, (size_t)n + 1)) || (rc = dalloc(&g->col, (size_t)m)) || (rc = dalloc(&g->w, (size_t)m)) ||
-      (rc = dalloc(&g->cw, (size_t)m)) ||
-      (rc = dalloc(&g->src, (size_t)m)) || (rc = dalloc(&g->ctl, 1)) || (rc = dalloc(&g->vflags, 4)) ||
+  if (g->device >= kPoolDevices) {
+    delete g;
+    return DAWN_ERR_CUDA;
+  }
+  pool_handle_created(g->device);
+  const int dev = g->device;
+  if ((rc = dalloc(dev, &g->row_ptr, (size_t)n + 1, s)) || (rc = dalloc(dev, &g->col, (size_t)m, s)) ||
+      (rc = dalloc(dev, &g->w, (size_t)m, s)) || (rc = dalloc(dev, &g->cw, (size_t)m, s)) ||
+      (rc = dalloc(dev, &g->src, (size_t)m, s)) || (rc = dalloc(dev, &g->ctl, 1, s)) ||
+      (rc = dalloc(dev, &g->vflags, 4, s)) ||
       (rc = copy_in(g->row_ptr, row_ptr, ((size_t)n + 1) * 4, inputs_on_device, s)) ||
       (rc = copy_in(g->col, col_idx, (size_t)m * 4, inputs_on_device, s)) ||
       (rc = copy_in(g->w, weights, (size_t)m * 4, inputs_on_device, s)) || (rc = validate(g, s))) {
-    release(g);
+    release(g, s, true);
     return rc;
   }
   if (cudaMemsetAsync(g->ctl, 0, sizeof(DeviceCtl), s) != cudaSuccess) {
-    release(g);
+    release(g, s, true);
     return DAWN_ERR_CUDA;
   }
   const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)n * 32 + 255) / 256, (int64_t)g->sms * 16));
@@ -558,11 +655,11 @@ int dawn_create_graph(int32_t n, int64_t m, const int32_t *row_ptr, const int32_
   const int eb = (int)std::max<int64_t>(1, std::min<int64_t>((m + 255) / 256, (int64_t)g->sms * 16));
   interleave_kernel<<<eb, 256, 0, s>>>(g->col, g->w, m, g->cw);
   if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
-    release(g);
+    release(g, s, true);
     return DAWN_ERR_CUDA;
   }
-  cudaFree(g->col);  // columns and weights now live in cw
-  cudaFree(g->w);
+  dfree(g->col, s);  // columns and weights now live in cw
+  dfree(g->w, s);
   g->col = nullptr;
   g->w = nullptr;
   g->last_stream = s;
@@ -578,7 +675,7 @@ int dawn_set_weights(dawn_graph g, const void *weights, int flags, void *stream)
   const uint32_t *src = (const uint32_t *)weights;
   int rc;
   if (!(flags & DAWN_WEIGHTS_ON_DEVICE) && g->m > 0) {  // host weights go through a device staging copy
-    if (!g->w && (rc = halloc(g, &g->w, (size_t)g->m))) return rc;
+    if (!g->w && (rc = halloc(g, &g->w, (size_t)g->m, s))) return rc;
     if ((rc = copy_in(g->w, weights, (size_t)g->m * 4, 0, s))) return rc;
     src = g->w;
   }
@@ -604,7 +701,10 @@ int dawn_set_weights(dawn_graph g, const void *weights, int flags, void *stream)
 int dawn_reserve(dawn_graph g, int32_t k) {
   if (!g || k < 1) return DAWN_ERR_INVALID;
   if (set_device(g)) return DAWN_ERR_CUDA;
-  return ensure_workspace(g, std::min(k, max_chunk(g)));
+  // allocated in the order of the handle's stream, then made usable on any
+  int rc = ensure_workspace(g, std::min(k, max_chunk(g)), g->last_stream);
+  if (rc == DAWN_OK && cudaStreamSynchronize(g->last_stream) != cudaSuccess) rc = DAWN_ERR_CUDA;
+  return rc;
 }
 
 int dawn_sssp(dawn_graph g, int32_t source, void *dist, int32_t *parent, int32_t *parent_edge, void *stream) {
@@ -646,7 +746,7 @@ int dawn_sssp_backward(dawn_graph g, const int32_t *parent_edge, const float *gr
   cudaStream_t s = (cudaStream_t)stream;
   const size_t n = (size_t)g->n;
   if (!g->bw_base) {
-    int rc = halloc(g, &g->bw_base, 32 + 16 * n);
+    int rc = halloc(g, &g->bw_base, 32 + 16 * n, s);
     if (rc) return rc;
     g->bw_edges = (unsigned long long *)g->bw_base;
     g->bw_cnt = (int32_t *)(g->bw_base + 32);  // inner [n], rem [n], par [n]
@@ -734,14 +834,17 @@ int dawn_set_option(dawn_graph g, int option, int64_t value) {
     case DAWN_OPT_TRACE_STEPS: {
       if (value < 0 || value > (1 << 24)) return DAWN_ERR_INVALID;
       if (set_device(g)) return DAWN_ERR_CUDA;
-      if (g->last_stream) cudaStreamSynchronize(g->last_stream);
-      cudaFree(g->trace);
+      cudaStream_t s = g->last_stream;
+      if (cudaStreamSynchronize(s) != cudaSuccess) return DAWN_ERR_CUDA;
+      dfree(g->trace, s);
       g->trace = nullptr;
       g->trace_cap = 0;
       if (value == 0) return DAWN_OK;
-      int rc = halloc(g, &g->trace, (size_t)value * 4);
+      int rc = halloc(g, &g->trace, (size_t)value * 4, s);
       if (rc) return rc;
-      if (cudaMemset(g->trace, 0, (size_t)value * 4 * sizeof(unsigned long long)) != cudaSuccess) return DAWN_ERR_CUDA;
+      if (cudaMemsetAsync(g->trace, 0, (size_t)value * 4 * sizeof(unsigned long long), s) != cudaSuccess ||
+          cudaStreamSynchronize(s) != cudaSuccess)
+        return DAWN_ERR_CUDA;
       g->trace_cap = (int32_t)value;
       return DAWN_OK;
     }
@@ -778,8 +881,8 @@ int dawn_graph_info(dawn_graph g, int32_t *n, int64_t *m, int *wtype) {
 void dawn_destroy(dawn_graph g) {
   if (!g) return;
   cudaSetDevice(g->device);
-  if (g->last_stream) cudaStreamSynchronize(g->last_stream);
-  release(g);
+  cudaStreamSynchronize(g->last_stream);  // the handle's work has finished: its memory can go back
+  release(g, g->last_stream, true);
 }
 
 }  // extern "C"
