@@ -466,29 +466,72 @@ def run_e2e(args, wl, device, world, tuning=None):
         if code:
             raise dawn.DawnError(code, "e2e solve")
 
-    def run(steps):
+    def run(steps, phases=None):
+        # phases: host milliseconds of each part of a step, and device
+        # milliseconds of its solves (events on the solve stream; they add
+        # nothing to the stream's work)
+        clock = lambda: time.perf_counter() * 1e3
+        t0 = clock()
         h = ingest()
+        first = clock() - t0
+        rows = []
         for k in range(steps):
+            t0 = clock()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+            ev[0].record(stream)
             solve(h)
+            ev[1].record(stream)
+            t1 = clock()
             h_next = ingest() if k + 1 < steps else None  # overlaps this step's solves
+            t2 = clock()
             finish(h)
+            t3 = clock()
             h = h_next
+            rows.append((t1 - t0, t2 - t1, t3 - t2, ev))
+        if phases is not None:
+            torch.cuda.synchronize()
+            phases["first_ingest_ms"] = first
+            phases["steps"] = [{"enqueue_ms": a, "ingest_next_ms": b, "status_and_destroy_ms": c,
+                                "device_ms": ev[0].elapsed_time(ev[1]),
+                                "device_gap_before_ms": rows[i - 1][3][1].elapsed_time(ev[0]) if i else None}
+                               for i, (a, b, c, ev) in enumerate(rows)]
 
     run(1)  # warm-up
     torch.cuda.synchronize()
     steps = max(1, min(args.steps, 3))
     barrier(world)
     torch.cuda.synchronize()
+    phases = {}
     t = time.perf_counter()
-    run(steps)
+    run(steps, phases)
     torch.cuda.synchronize()
     el = time.perf_counter() - t
     barrier(world)
     el = max_over_ranks(el, world)
     h2d = wl.row_ptr.nbytes + wl.col.nbytes + wl.weights.nbytes
     d2h = h_dist.numel() * 4 + h_par.numel() * 4
+    # after the timed region: each direction's copies alone, on an idle GPU,
+    # to show how much of a step the host link needs
+    a_ev, b_ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a_ev.record(stream)
+    h_dist.copy_(dist, non_blocking=True)
+    h_par.copy_(par, non_blocking=True)
+    b_ev.record(stream)
+    torch.cuda.synchronize()
+    d2h_ms = a_ev.elapsed_time(b_ev)
+    g_dev = [torch.empty(x.numel(), dtype=x.dtype, device=device) for x in (rp, cl, w)]
+    a_ev.record(stream)
+    for dst, src in zip(g_dev, (rp, cl, w)):
+        dst.copy_(src, non_blocking=True)
+    b_ev.record(stream)
+    torch.cuda.synchronize()
+    h2d_ms = a_ev.elapsed_time(b_ev)
+    del g_dev
     return {"value": S * world * wl.e_wcc / (el / steps) / 1e9, "unit": "GTEPS", "h2d_bytes_per_step": int(h2d),
-            "d2h_bytes_per_step": int(d2h), "steps": steps, "ms_per_step": el / steps * 1e3}
+            "d2h_bytes_per_step": int(d2h), "steps": steps, "ms_per_step": el / steps * 1e3,
+            "copies_alone_ms": {"d2h": d2h_ms, "h2d": h2d_ms, "d2h_gbs": d2h / d2h_ms / 1e6,
+                                "h2d_gbs": h2d / h2d_ms / 1e6},
+            "phases": phases}
 
 
 def cpu_baseline(wl, budget_s: float = 20.0, gpu_dist=None, single_core: bool = True):
@@ -701,6 +744,12 @@ def leg_diff(args, device=0):
     def bwd():
         dawn.dawn_sssp_backward(g.handle, pe, grad_dist, grad_w)
 
+    leaf = torch.zeros(wl.n, dtype=torch.float32, device="cuda", requires_grad=True)
+
+    def loss_only():  # the same loss and its backward on a leaf tensor: PyTorch's share of an autograd step
+        leaf.grad = None
+        (leaf[tg] * cf).sum().backward()
+
     def c_abi_fwd_bwd():
         dawn.dawn_sssp(g.handle, 0, dist, None, pe)
         dawn.dawn_sssp_backward(g.handle, pe, grad_dist, grad_w)
@@ -708,7 +757,7 @@ def leg_diff(args, device=0):
     with Clocks(device) as clk:
         for name, fn in (("plain_sssp_s", plain), ("backward_kernel_s", bwd), ("c_abi_forward_backward_s", c_abi_fwd_bwd),
                          ("autograd_forward_s", fwd), ("autograd_forward_backward_s", fwd_bwd),
-                         ("autograd_forward_backward_nosync_s", fwd_bwd_nosync)):
+                         ("autograd_forward_backward_nosync_s", fwd_bwd_nosync), ("autograd_loss_only_s", loss_only)):
             times[name] = float(np.median(timed_calls(fn, reps_for(fn, 0.4, lo=20, hi=2000), flush=flush, warm=3)))
         g.check()
         # the same autograd step (no status read) captured once in a CUDA
@@ -742,6 +791,9 @@ def leg_diff(args, device=0):
                 "autograd_fb_over_plain": times["autograd_forward_backward_s"] / times["plain_sssp_s"],
                 "autograd_fb_nosync_over_plain": times["autograd_forward_backward_nosync_s"] / times["plain_sssp_s"],
                 "autograd_fb_graph_over_plain": times["autograd_forward_backward_graph_s"] / times["plain_sssp_s"],
+                # the eager step less the loss's own autograd cost (a leaf tensor in place of the solver)
+                "autograd_fb_nosync_less_loss_over_plain":
+                    (times["autograd_forward_backward_nosync_s"] - times["autograd_loss_only_s"]) / times["plain_sssp_s"],
                 "graph_grad_max_diff_over_max": graph_grad_diff,
                 "timing": "median of per-call CUDA events", "clocks": clk.summary(), "l2": l2note,
                 "config": {"workload": wl.name, "n": wl.n, "m": wl.m, "source": 0, "targets": len(wl.extra["targets"]),

@@ -59,6 +59,7 @@ static_assert(kTile < kMark && kEdgesPerLane <= 4, "entry indices of a tile fit 
 struct WarpTile {
   uint32_t ebase[kTile + 1];  // per entry: CSR index of its edge at virtual offset 0 (mod 2^32)
   uint32_t dkey[kTile + 1];   // per entry: current distance key of its vertex
+  uint32_t vert[kTile + 1];   // per entry: its vertex (the tail of its edges)
   int32_t own[kTile];         // owning entry (relative index) of every virtual edge
 };
 
@@ -469,12 +470,18 @@ __device__ __forceinline__ unsigned relax_edges(const GovmParams &p, WarpTile &w
   // Relax.  A candidate that beats the distance read marks beta (the thread
   // whose atomicMin strictly lowers a distance always read a larger value, so
   // every strict improvement is marked); equal-distance candidates with a
-  // lower edge index only update the parent.
+  // lower edge index only update the parent.  The low half of a candidate is
+  // its edge when the call wants parent_edge, else the edge's tail: CSR edge
+  // indices grow with the tail, so for equal keys both select the same parent
+  // vertex (distances and marks do not depend on the low half), and the
+  // output unpack then reads the parent without a gather of the edge's tail.
   uint32_t ckey[kEdgesPerLane];
   unsigned need = 0;
 #pragma unroll
   for (int r = 0; r < kEdgesPerLane; ++r) {
-    ckey[r] = Key<WT>::add(wt.dkey[(jpack >> (8 * r)) & 0xFFu], cw[r].y);
+    const uint32_t j = (jpack >> (8 * r)) & 0xFFu;
+    ckey[r] = Key<WT>::add(wt.dkey[j], cw[r].y);
+    if (p.parent_edge == nullptr) eidx[r] = wt.vert[j];
     const unsigned long long cand = ((unsigned long long)ckey[r] << 32) | eidx[r];
     if ((valid & (1u << r)) && cand < curst[r] && curst[r] != kSourceState) need |= 1u << r;
   }
@@ -533,17 +540,20 @@ __device__ __forceinline__ void relax_tile(const GovmParams &p, WarpTile &wt, in
   unsigned long long f0 = ~0ull, f1 = ~0ull;
   if (j0 < nent) {
     wt.ebase[j0] = e0.z;
+    wt.vert[j0] = e0.w;
     if (j0 > 0 && e0.y >= x0 && e0.y < x0 + (uint32_t)kTile) wt.own[e0.y - x0] = kMark | j0;
     f0 = ld_relaxed_u64(st + e0.w);
   }
   if (j1 < nent) {
     wt.ebase[j1] = e1.z;
+    wt.vert[j1] = e1.w;
     if (e1.y >= x0 && e1.y < x0 + (uint32_t)kTile) wt.own[e1.y - x0] = kMark | j1;
     f1 = ld_relaxed_u64(st + e1.w);
   }
   for (int32_t j = lane + 64; j < nent; j += 32) {  // tiles of many short rows
     const uint4 en = __ldcg(q + ia + j);
     wt.ebase[j] = en.z;
+    wt.vert[j] = en.w;
     wt.dkey[j] = (uint32_t)(ld_relaxed_u64(st + en.w) >> 32);
     if (en.y >= x0 && en.y < x0 + (uint32_t)kTile) wt.own[en.y - x0] = kMark | j;
   }
@@ -575,11 +585,13 @@ __device__ __forceinline__ void relax_tile(const GovmParams &p, WarpTile &wt, in
 // is not expanded now: it is in the next frontier and is expanded there with
 // a key no larger.  Counters: `marked` (the vertices consumed), `front`
 // (those with an out-edge), `edges` (their out-edges) and `skipped` (the
-// out-edges of the vertices not expanded).  Returns whether this warp made
-// any strict improvement (a mark in bn).
+// out-edges of the vertices not expanded).  `first_bits` is the lane's word
+// of the first round, which the caller loads before its stop test.  Returns
+// whether this warp made any strict improvement (a mark in bn).
 template <int WT>
-__device__ bool direct_step(const GovmParams &p, uint32_t *bm, uint32_t *bn, WarpTile &wt, unsigned long long &marked,
-                            unsigned long long &front, unsigned long long &edges, unsigned long long &skipped) {
+__device__ bool direct_step(const GovmParams &p, uint32_t *bm, uint32_t *bn, uint32_t first_bits, WarpTile &wt,
+                            unsigned long long &marked, unsigned long long &front, unsigned long long &edges,
+                            unsigned long long &skipped) {
   const int lane = threadIdx.x & 31;
   const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -593,7 +605,7 @@ __device__ bool direct_step(const GovmParams &p, uint32_t *bm, uint32_t *bn, War
     const int64_t w = base + (int64_t)lane * nwarps;  // this lane's word
     uint32_t bits = 0;
     if (w < p.words) {
-      bits = __ldcg(bm + w);
+      bits = base == gwarp ? first_bits : __ldcg(bm + w);  // the first round's word was loaded by the caller
       if (bits) bm[w] = 0u;  // consumed: this bitmap receives the marks of the next step
     }
     const uint32_t pc = __popc(bits);
@@ -656,6 +668,7 @@ __device__ bool direct_step(const GovmParams &p, uint32_t *bm, uint32_t *bn, War
       __syncwarp();
       wt.ebase[lane] = rs - off;
       wt.dkey[lane] = (uint32_t)(f >> 32);
+      wt.vert[lane] = (uint32_t)v;
       __syncwarp();
       for (uint32_t x0 = 0; x0 < D; x0 += kTile) {  // warp-uniform
         const uint32_t xend = min(x0 + (uint32_t)kTile, D);
@@ -687,7 +700,10 @@ __device__ bool direct_step(const GovmParams &p, uint32_t *bm, uint32_t *bn, War
 // DIRECT selects the step form (p.direct): direct steps (the frontier read
 // from the bitmap, one barrier per step) or queue steps (relax tiles, then
 // build).  Each form is its own instantiation, so neither pays the other's
-// registers.
+// registers.  A call without a parent_edge output packs each state's parent
+// as the edge's tail instead of the edge (relax_edges), so the output unpack
+// needs no gather of the tail; that choice is a run-time flag, not a further
+// instantiation, because the instantiated form measured slower.
 template <int WT, int MINB, bool DIRECT>
 __global__ void __launch_bounds__(kBlockThreads, MINB) govm_kernel(GovmParams p) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -755,6 +771,11 @@ __global__ void __launch_bounds__(kBlockThreads, MINB) govm_kernel(GovmParams p)
   if (DIRECT) {  // one barrier per step; the frontier stays a bitmap
     unsigned long long front = 0, edges = 0;
     for (;; ++step) {
+      // this lane's first frontier word, loaded before the stop test so that
+      // the two round trips overlap
+      uint32_t *bm_cur = p.bitmap + (size_t)(step & 1) * p.words;
+      const long long w0 = (gtid >> 5) + (long long)lane * (gsize >> 5);
+      const uint32_t first_bits = w0 < p.words ? __ldcg(bm_cur + w0) : 0u;
       // stop after a step that lowered no distance (its marks would be the
       // next frontier)
       if (step > 0 && ld_volatile_i32((const int *)&ctl->marks[(step - 1) % 3]) == 0) {
@@ -777,9 +798,8 @@ __global__ void __launch_bounds__(kBlockThreads, MINB) govm_kernel(GovmParams p)
         ctl->marks[(step + 1) % 3] = 0u;  // set in step + 1, read two steps from now
       }
       const unsigned long long f0 = front, e0 = edges;
-      const bool any = direct_step<WT>(p, p.bitmap + (size_t)(step & 1) * p.words,
-                                       p.bitmap + (size_t)((step + 1) & 1) * p.words, sh.wt[warp],
-                                       step == 0 ? seeded : updates, front, edges, skipped);
+      const bool any = direct_step<WT>(p, bm_cur, p.bitmap + (size_t)((step + 1) & 1) * p.words, first_bits,
+                                       sh.wt[warp], step == 0 ? seeded : updates, front, edges, skipped);
       if (any && lane == 0) sh.any_mark = 1;
       if (p.trace) {  // traced solves keep the cumulative counters current per step
         unsigned long long df = front - f0, de = edges - e0;
@@ -900,7 +920,7 @@ __global__ void __launch_bounds__(kBlockThreads, MINB) govm_kernel(GovmParams p)
         const uint32_t key = (uint32_t)(s[u] >> 32), e = (uint32_t)s[u];
         pv[u] = -1;
         if (p.parent && idx < total && key != Key<WT>::inf)
-          pv[u] = e == kNoEdge ? (int32_t)(idx % p.n) : __ldg(p.src + e);
+          pv[u] = e == kNoEdge ? (int32_t)(idx % p.n) : p.parent_edge == nullptr ? (int32_t)e : __ldg(p.src + e);
       }
 #pragma unroll
       for (int u = 0; u < kU; ++u) {
