@@ -3,7 +3,8 @@ stream-ordered pool per device.  A graph created on its own stream while
 another handle's solves run, then the old handle destroyed (a serving loop),
 gives the oracle's results; a destroyed handle's memory serves the next
 handle and goes back to the device with the last handle; allocation is
-refused while the stream is being captured."""
+refused while the stream is being captured; host threads that create, solve
+and destroy their own graphs at the same time share the pool safely."""
 import gc
 
 import numpy as np
@@ -118,3 +119,42 @@ def test_allocation_refused_during_capture_then_reserve(dawn):
     d_ref, _, _ = oracle.sssp(wl.row_ptr, wl.col, wl.weights, src)
     assert np.array_equal(dist.cpu().numpy(), d_ref)
     g.close()
+
+
+def test_handles_created_and_destroyed_on_several_threads(dawn):
+    # host threads share the library's pool: each creates, solves and
+    # destroys its own graphs on its own stream while the others do the same
+    import threading
+    wls = [[gg.rmat_u32(12, 8, nsrc=2, seed=60 + 10 * t + i) for i in range(3)] for t in range(4)]
+    results, errors = {}, []
+
+    def work(t):
+        try:
+            s = torch.cuda.Stream()
+            for i, wl in enumerate(wls[t]):
+                h = host_create(dawn, wl, s)
+                dawn.dawn_set_option(h, dawn.DAWN_OPT_SMALL_PATH, dawn.DAWN_SMALL_NEVER)
+                dist = torch.empty((2, wl.n), dtype=torch.uint32, device="cuda")
+                par = torch.empty((2, wl.n), dtype=torch.int32, device="cuda")
+                s.wait_stream(torch.cuda.current_stream())  # the outputs' allocation is ordered before the solves
+                for j, src in enumerate(wl.sources):
+                    dawn.dawn_sssp(h, int(src), dist[j], par[j], None, s)
+                assert dawn.dawn_status(h, True) == 0
+                dawn.dawn_destroy(h)
+                results[(t, i)] = (dist.cpu().numpy(), par.cpu().numpy())
+        except Exception as e:  # reported by the main thread
+            errors.append(e)
+
+    threads = [threading.Thread(target=work, args=(t,)) for t in range(4)]
+    for th in threads:
+        th.start()
+    for th in threads:
+        th.join()
+    assert not errors, errors
+    for t in range(4):
+        for i, wl in enumerate(wls[t]):
+            d, p = results[(t, i)]
+            for j, src in enumerate(wl.sources):
+                d_ref, p_ref, _ = oracle.sssp(wl.row_ptr, wl.col, wl.weights, int(src))
+                assert np.array_equal(d[j], d_ref), (t, i, j)
+                assert np.array_equal(p[j], p_ref), (t, i, j)
