@@ -106,9 +106,10 @@ typedef struct {
  * memory pool per device that the library owns; no call allocates with
  * cudaMalloc or frees with cudaFree, so no allocation or free synchronises
  * the device.
- * Memory a handle frees stays in the pool for the next allocation and goes
- * back to the device when the last handle on it is destroyed.  Allocations
- * are refused (DAWN_ERR_CUDA) on a stream that is being captured.
+ * Memory a handle frees stays in the pool and serves later allocations
+ * without mapping new memory; dawn_trim_memory returns it to the devices.
+ * Allocations are refused (DAWN_ERR_CUDA) on a stream that is being
+ * captured.
  * Errors: DAWN_ERR_INVALID (malformed input), DAWN_ERR_OOM, DAWN_ERR_CUDA.
  */
 int dawn_create_graph(int32_t n, int64_t m, const int32_t *row_ptr, const int32_t *col_idx,
@@ -425,9 +426,19 @@ int dawn_sssp_noalloc(dawn_graph g, int32_t source, void *dist, int32_t *parent,
 const char *dawn_status_string(int code);
 
 /* Free the graph and its device memory.  Waits for the handle's last stream,
- * then returns its buffers to the library's pool (see dawn_create_graph).
+ * then returns its buffers to the library's pool (see dawn_create_graph),
+ * where they stay for later handles until dawn_trim_memory.
  * NULL is allowed (plumbing). */
 void dawn_destroy(dawn_graph g);
+
+/* Return to the devices the memory of the library's pools that no handle
+ * holds (memory freed by dawn_destroy, by a workspace that grew, or by a
+ * replaced trace buffer).  Handles stay valid; their later allocations map
+ * memory again.  A pool that grows while solves run maps new memory, which
+ * can stall those solves, so a process that creates and destroys graphs in
+ * a loop is best left untrimmed until it idles.  DAWN_ERR_CUDA on a CUDA
+ * error (plumbing). */
+int dawn_trim_memory(void);
 
 #ifdef __cplusplus
 }

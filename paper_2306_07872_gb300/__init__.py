@@ -12,5 +12,5 @@ from .dawn import (  # noqa: F401
     DAWN_W_U32, DAWN_WEIGHTS_DEFER_CHECK, DAWN_WEIGHTS_ON_DEVICE, EXPORTS, DawnError, DawnSSSP, Graph, dawn_autotune, dawn_create_graph, dawn_destroy, dawn_get_stats,
     dawn_get_trace, dawn_graph_info, dawn_msssp,
     dawn_reserve, dawn_set_option, dawn_set_weights, dawn_sssp, dawn_sssp_backward, dawn_sssp_noalloc, dawn_sssp_roots, dawn_status,
-    dawn_status_string, load_library,
+    dawn_status_string, dawn_trim_memory, load_library,
 )

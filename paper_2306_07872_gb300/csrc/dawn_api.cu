@@ -260,12 +260,12 @@ int cuda_fail(cudaError_t e) {
 // device, so a serving loop that builds the next graph while the current
 // one's solves run, then destroys the old handle, leaves no idle gap on the
 // GPU.  Reuse across streams happens only once a free has completed in its
-// stream's order (no hidden cross-stream dependencies).  When the last
-// handle on a device is destroyed, the pool is trimmed and its memory goes
-// back to the device.
+// stream's order (no hidden cross-stream dependencies).  Freed memory stays
+// in the pool until dawn_trim_memory: growing a pool maps new memory, which
+// can stall solves running at the same time, so a loop that creates and
+// destroys graphs reaches a steady state with no mapping at all.
 struct DevicePool {
   cudaMemPool_t pool = nullptr;
-  int live = 0;  // handles alive on the device
 };
 constexpr int kPoolDevices = 64;
 std::mutex g_pool_mutex;
@@ -286,7 +286,7 @@ cudaMemPool_t device_pool(int device) {
       cudaGetLastError();
       return nullptr;
     }
-    uint64_t keep = UINT64_MAX;  // keep freed memory for reuse until the trim
+    uint64_t keep = UINT64_MAX;  // keep freed memory for reuse until dawn_trim_memory
     int off = 0;
     if (cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess ||
         cudaMemPoolSetAttribute(pool, cudaMemPoolReuseAllowInternalDependencies, &off) != cudaSuccess) {
@@ -297,18 +297,6 @@ cudaMemPool_t device_pool(int device) {
     d.pool = pool;
   }
   return d.pool;
-}
-
-void pool_handle_created(int device) {
-  std::lock_guard<std::mutex> lock(g_pool_mutex);
-  ++g_pools[device].live;
-}
-
-// Called after the handle's frees were enqueued and its stream synchronised.
-void pool_handle_destroyed(int device) {
-  std::lock_guard<std::mutex> lock(g_pool_mutex);
-  DevicePool &d = g_pools[device];
-  if (--d.live == 0 && d.pool) cudaMemPoolTrimTo(d.pool, 0);
 }
 
 // Stream-ordered allocation on `stream` from the device's pool: usable by
@@ -553,8 +541,10 @@ int validate(dawn_graph g, cudaStream_t stream, bool wait = true) {
 }
 
 // Frees every device buffer of the handle on `stream` (which the handle's
-// work has been ordered on or has finished) and deletes it.
-void release(dawn_graph g, cudaStream_t stream, bool counted) {
+// work has been ordered on or has finished), waits until the frees have
+// completed (so a later dawn_trim_memory can return the memory) and deletes
+// the handle.
+void release(dawn_graph g, cudaStream_t stream) {
   free_workspace(g, stream);
   dfree(g->row_ptr, stream);
   dfree(g->col, stream);
@@ -565,12 +555,8 @@ void release(dawn_graph g, cudaStream_t stream, bool counted) {
   dfree(g->ctl, stream);
   dfree(g->vflags, stream);
   dfree(g->bw_base, stream);
-  const int device = g->device;
   delete g;
-  if (counted) {
-    cudaStreamSynchronize(stream);  // the frees have completed: the trim can return them
-    pool_handle_destroyed(device);
-  }
+  cudaStreamSynchronize(stream);
 }
 
 }  // namespace
@@ -634,7 +620,6 @@ int dawn_create_graph(int32_t n, int64_t m, const int32_t *row_ptr, const int32_
     delete g;
     return DAWN_ERR_CUDA;
   }
-  pool_handle_created(g->device);
   const int dev = g->device;
   if ((rc = dalloc(dev, &g->row_ptr, (size_t)n + 1, s)) || (rc = dalloc(dev, &g->col, (size_t)m, s)) ||
       (rc = dalloc(dev, &g->w, (size_t)m, s)) || (rc = dalloc(dev, &g->cw, (size_t)m, s)) ||
@@ -643,11 +628,11 @@ int dawn_create_graph(int32_t n, int64_t m, const int32_t *row_ptr, const int32_
       (rc = copy_in(g->row_ptr, row_ptr, ((size_t)n + 1) * 4, inputs_on_device, s)) ||
       (rc = copy_in(g->col, col_idx, (size_t)m * 4, inputs_on_device, s)) ||
       (rc = copy_in(g->w, weights, (size_t)m * 4, inputs_on_device, s)) || (rc = validate(g, s))) {
-    release(g, s, true);
+    release(g, s);
     return rc;
   }
   if (cudaMemsetAsync(g->ctl, 0, sizeof(DeviceCtl), s) != cudaSuccess) {
-    release(g, s, true);
+    release(g, s);
     return DAWN_ERR_CUDA;
   }
   const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(((int64_t)n * 32 + 255) / 256, (int64_t)g->sms * 16));
@@ -655,7 +640,7 @@ int dawn_create_graph(int32_t n, int64_t m, const int32_t *row_ptr, const int32_
   const int eb = (int)std::max<int64_t>(1, std::min<int64_t>((m + 255) / 256, (int64_t)g->sms * 16));
   interleave_kernel<<<eb, 256, 0, s>>>(g->col, g->w, m, g->cw);
   if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) {
-    release(g, s, true);
+    release(g, s);
     return DAWN_ERR_CUDA;
   }
   dfree(g->col, s);  // columns and weights now live in cw
@@ -882,7 +867,23 @@ void dawn_destroy(dawn_graph g) {
   if (!g) return;
   cudaSetDevice(g->device);
   cudaStreamSynchronize(g->last_stream);  // the handle's work has finished: its memory can go back
-  release(g, g->last_stream, true);
+  release(g, g->last_stream);
+}
+
+int dawn_trim_memory(void) {
+  std::lock_guard<std::mutex> lock(g_pool_mutex);
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return DAWN_ERR_CUDA;
+  int rc = DAWN_OK;
+  for (int d = 0; d < kPoolDevices; ++d) {
+    if (!g_pools[d].pool) continue;
+    if (cudaSetDevice(d) != cudaSuccess || cudaMemPoolTrimTo(g_pools[d].pool, 0) != cudaSuccess) {
+      cudaGetLastError();
+      rc = DAWN_ERR_CUDA;
+    }
+  }
+  if (cudaSetDevice(dev) != cudaSuccess) rc = DAWN_ERR_CUDA;
+  return rc;
 }
 
 }  // extern "C"

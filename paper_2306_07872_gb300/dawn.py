@@ -37,7 +37,7 @@ DAWN_WEIGHTS_ON_DEVICE, DAWN_WEIGHTS_DEFER_CHECK = 1, 2
 
 EXPORTS = ("dawn_create_graph", "dawn_set_weights", "dawn_reserve", "dawn_sssp", "dawn_msssp", "dawn_sssp_roots",
            "dawn_sssp_backward", "dawn_status", "dawn_get_stats", "dawn_set_option", "dawn_get_trace", "dawn_graph_info",
-           "dawn_status_string", "dawn_destroy", "dawn_sssp_noalloc", "dawn_autotune")
+           "dawn_status_string", "dawn_destroy", "dawn_trim_memory", "dawn_sssp_noalloc", "dawn_autotune")
 
 
 class DawnError(RuntimeError):
@@ -84,6 +84,7 @@ def load_library(path: str = LIB_PATH):
         "dawn_graph_info": ([vp, ctypes.POINTER(i32), ctypes.POINTER(i64), ctypes.POINTER(c_int)], c_int),
         "dawn_status_string": ([c_int], ctypes.c_char_p),
         "dawn_destroy": ([vp], None),
+        "dawn_trim_memory": ([], c_int),
         "dawn_sssp_noalloc": ([vp, i32, vp, vp, vp, vp, vp], c_int),
         "dawn_autotune": ([vp, c_int, vp, i32, i32, vp, ctypes.POINTER(_Tuning)], c_int),
     }
@@ -261,6 +262,11 @@ def dawn_status_string(code: int) -> str:
 def dawn_destroy(g: int):
     if g:
         load_library().dawn_destroy(ctypes.c_void_p(g))
+
+
+def dawn_trim_memory():
+    """Return the library pools' unused device memory to the devices."""
+    _check(load_library().dawn_trim_memory(), "dawn_trim_memory")
 
 
 # ----------------------------------------------------------------- convenience

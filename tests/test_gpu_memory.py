@@ -2,7 +2,8 @@
 stream-ordered pool per device.  A graph created on its own stream while
 another handle's solves run, then the old handle destroyed (a serving loop),
 gives the oracle's results; a destroyed handle's memory serves the next
-handle and goes back to the device with the last handle; allocation is
+handle, stays in the pool and goes back to the device on dawn_trim_memory;
+allocation is
 refused while the stream is being captured; host threads that create, solve
 and destroy their own graphs at the same time share the pool safely."""
 import gc
@@ -77,7 +78,8 @@ def test_destroyed_handle_memory_is_reused_then_returned(dawn):
         assert np.array_equal(dist.cpu().numpy(), d_ref)
         return h
 
-    gc.collect()  # handles of earlier tests are gone, so the pool starts empty
+    gc.collect()  # handles of earlier tests are gone
+    dawn.dawn_trim_memory()  # and the pool holds nothing
     free0 = free_bytes()
     a = make()
     b = make()
@@ -90,7 +92,13 @@ def test_destroyed_handle_memory_is_reused_then_returned(dawn):
     assert free_ab - free_bytes() < per_handle / 2
     dawn.dawn_destroy(b)
     dawn.dawn_destroy(c)
-    assert free_bytes() >= free0 - 8 * MB  # the last handle's destroy trimmed the pool
+    free_kept = free_bytes()
+    assert free_kept < free0 - per_handle  # with no handle left the pool still holds the memory
+    dawn.dawn_trim_memory()
+    assert free_bytes() >= free0 - 8 * MB  # and gives it back when trimmed
+    h = make()  # a trimmed pool serves new handles as before
+    dawn.dawn_destroy(h)
+    dawn.dawn_trim_memory()
 
 
 def test_allocation_refused_during_capture_then_reserve(dawn):
