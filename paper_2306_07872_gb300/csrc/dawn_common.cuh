@@ -115,7 +115,7 @@ int govm_max_blocks_per_sm(int wtype, int ctas_per_sm);
 constexpr int kSmallThreads = 1024;
 constexpr int kSmallWarps = kSmallThreads / 32;
 struct SmallLayout {  // byte offsets in the block's dynamic shared memory
-  size_t state, bitmap, front, scan, row_ptr, cw, total;
+  size_t state, bitmap, front, scan, hasout, row_ptr, cw, total;
 };
 // compact: 32-bit keys and 16-bit frontier ids (no parents, weights >= 0,
 // n <= 65,536), half the shared memory of the packed form.

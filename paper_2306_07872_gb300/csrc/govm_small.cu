@@ -9,12 +9,14 @@
 // instances runs as an ordinary (non-cooperative) launch of one block each.
 //   relax  a group of `group` threads (a power of two near the average
 //          degree) per frontier vertex, its threads over the vertex's
-//          out-edges; the vertex's distance is read in place (Algorithm 2); a candidate
+//          out-edges (two per thread and round when the CSR is read from
+//          L2); the vertex's distance is read in place (Algorithm 2); a candidate
 //          that beats alpha[t] updates it with a packed 64-bit atomicMin in
 //          shared memory, and marks beta[t] when that atomic strictly lowered
 //          the distance;
-//   build  beta is compacted into delta (vertices with an out-edge) by a
-//          block-wide prefix sum and cleared.
+//   build  beta is compacted into delta (vertices with an out-edge, read
+//          from a bitmap built once per block, so the build touches shared
+//          memory only) by a block-wide prefix sum and cleared.
 // The same (distance, lowest parent edge) fixpoint as the persistent kernel
 // results: both are exact minima of the packed keys.
 // Compact form, for solves that want no parents on graphs with non-negative
@@ -42,7 +44,8 @@ __host__ __device__ SmallLayout small_layout(int32_t n, int64_t m, bool csr, boo
   L.bitmap = L.state + round16((compact ? 4 : 8) * (size_t)n);
   L.front = L.bitmap + round16(4 * (size_t)((n + 31) / 32));
   L.scan = L.front + round16((compact ? 2 : 4) * (size_t)n);
-  L.row_ptr = L.scan + round16(4 * (size_t)(2 * kSmallWarps + 2));
+  L.hasout = L.scan + round16(4 * (size_t)(2 * kSmallWarps + 2));
+  L.row_ptr = L.hasout + round16(4 * (size_t)((n + 31) / 32));
   L.cw = L.row_ptr + (csr ? round16(4 * ((size_t)n + 1)) : 0);
   L.total = L.cw + (csr ? round16(8 * (size_t)m) : 0);
   return L;
@@ -83,31 +86,33 @@ __device__ __forceinline__ int32_t block_prefix(int32_t x, int32_t *sc, int32_t 
 }
 
 // delta <- beta restricted to vertices with an out-edge; beta <- {}.  Returns
-// the new frontier size (block-uniform); adds its out-edges to *edges and the
-// marked vertices to *marks (thread-local partial sums).  Each thread owns a
-// contiguous range of vertices, so all threads share the work however few
-// bitmap words there are.
+// the new frontier size (block-uniform) and adds the marked vertices to
+// *marks (a thread-local partial sum).  `ho` is the bitmap of vertices with
+// an out-edge, built once per block, so the build reads shared memory only.
+// Each thread owns a contiguous range of bitmap words, so the frontier lists
+// its vertices in increasing order.
 template <typename FrontT>
-__device__ int32_t small_build(int32_t n, const int32_t *rp, uint32_t *bm, FrontT *front, int32_t *sc,
-                               unsigned long long *edges, unsigned long long *marks) {
-  const int32_t per = (n + (int32_t)blockDim.x - 1) / (int32_t)blockDim.x;
-  const int32_t v0 = (int32_t)threadIdx.x * per, v1 = min(v0 + per, n);
+__device__ int32_t small_build(int32_t n, const uint32_t *ho, uint32_t *bm, FrontT *front, int32_t *sc,
+                               unsigned long long *marks) {
+  const int32_t words = (n + 31) / 32;
+  const int32_t per = (words + (int32_t)blockDim.x - 1) / (int32_t)blockDim.x;
+  const int32_t w0 = min((int32_t)threadIdx.x * per, words), w1 = min(w0 + per, words);
   int32_t mine = 0;
-  for (int32_t v = v0; v < v1; ++v) {
-    if (!(bm[v >> 5] & (1u << (v & 31)))) continue;
-    ++*marks;
-    const int32_t d = rp[v + 1] - rp[v];
-    if (d > 0) {
-      ++mine;
-      *edges += (unsigned long long)d;
-    }
+  for (int32_t w = w0; w < w1; ++w) {
+    const uint32_t b = bm[w];
+    *marks += __popc(b);
+    mine += __popc(b & ho[w]);
   }
   int32_t total = 0;
   int32_t at = block_prefix(mine, sc, &total);
-  for (int32_t v = v0; v < v1; ++v)
-    if ((bm[v >> 5] & (1u << (v & 31))) && rp[v + 1] > rp[v]) front[at++] = (FrontT)v;
-  __syncthreads();  // every thread has read beta
-  for (int32_t w = threadIdx.x; w < (n + 31) / 32; w += blockDim.x) bm[w] = 0u;
+  for (int32_t w = w0; w < w1; ++w) {
+    uint32_t b = bm[w] & ho[w];
+    bm[w] = 0u;  // only this thread reads its words
+    while (b) {
+      front[at++] = (FrontT)(w * 32 + __ffs(b) - 1);
+      b &= b - 1;
+    }
+  }
   __syncthreads();
   return total;
 }
@@ -121,6 +126,7 @@ __global__ void __launch_bounds__(kSmallThreads, COMPACT ? 2 : 1) govm_small_ker
   unsigned long long *st = reinterpret_cast<unsigned long long *>(smem + L.state);  // packed form
   uint32_t *sk = reinterpret_cast<uint32_t *>(smem + L.state);                      // compact form: keys
   uint32_t *bm = reinterpret_cast<uint32_t *>(smem + L.bitmap);
+  uint32_t *ho = reinterpret_cast<uint32_t *>(smem + L.hasout);
   FrontT *front = reinterpret_cast<FrontT *>(smem + L.front);
   int32_t *sc = reinterpret_cast<int32_t *>(smem + L.scan);
   const int tid = threadIdx.x, lane = tid & 31;
@@ -144,7 +150,10 @@ __global__ void __launch_bounds__(kSmallThreads, COMPACT ? 2 : 1) govm_small_ker
     if (COMPACT) sk[v] = Key<WT>::inf;
     else st[v] = kInfState;
   }
-  for (int32_t w = tid; w < (n + 31) / 32; w += blockDim.x) bm[w] = 0u;
+  for (int32_t w = tid; w < (n + 31) / 32; w += blockDim.x) {
+    bm[w] = 0u;
+    ho[w] = 0u;
+  }
   const int32_t *rp = p.row_ptr;
   const uint2 *cw = p.cw;
   if (csr_in_smem) {
@@ -156,6 +165,9 @@ __global__ void __launch_bounds__(kSmallThreads, COMPACT ? 2 : 1) govm_small_ker
     cw = scw;
   }
   __syncthreads();
+  // vertices with an out-edge (the build keeps only those in delta)
+  for (int32_t v = tid; v < n; v += blockDim.x)
+    if (rp[v + 1] > rp[v]) atomicOr(ho + (v >> 5), 1u << (v & 31));
 
   // 2. Seeds: alpha[s] = 0, s enters beta.
   const int32_t nseeds = p.roots_mode ? p.nseeds : 1;
@@ -171,8 +183,7 @@ __global__ void __launch_bounds__(kSmallThreads, COMPACT ? 2 : 1) govm_small_ker
   }
   __syncthreads();
   unsigned long long fsum = 0, esum = 0, seeded = 0, updates = 0;
-  unsigned long long edges_cur = 0;  // this thread's share of the current frontier's out-edges
-  int32_t count = small_build(n, rp, bm, front, sc, &edges_cur, &seeded);
+  int32_t count = small_build(n, ho, bm, front, sc, &seeded);
 
   // 3. GOVM steps.
   long long step = 0;
@@ -183,14 +194,13 @@ __global__ void __launch_bounds__(kSmallThreads, COMPACT ? 2 : 1) govm_small_ker
       break;
     }
     fsum += (unsigned long long)count;
-    esum += edges_cur;
     for (int32_t fi = gid; fi < count; fi += ngroups) {
       const int32_t u = front[fi];
       // alpha[u] in place, as Algorithm 2 reads it
       const uint32_t du = COMPACT ? sk[u] : (uint32_t)(st[u] >> 32);
       const int32_t b = rp[u], e = rp[u + 1];
-      for (int32_t x = b + glane; x < e; x += group) {
-        const uint2 c = cw[x];
+      if (glane == 0) esum += (unsigned long long)(e - b);
+      auto relax = [&](uint2 c, int32_t x) {
         const uint32_t t = c.x;
         const uint32_t ckey = Key<WT>::add(du, c.y);
         if (COMPACT) {  // keys alone: a source's zero key is never beaten (weights >= 0)
@@ -206,11 +216,21 @@ __global__ void __launch_bounds__(kSmallThreads, COMPACT ? 2 : 1) govm_small_ker
             if (ckey < (uint32_t)(old >> 32)) atomicOr(bm + (t >> 5), 1u << (t & 31));
           }
         }
+      };
+      if (csr_in_smem) {
+        for (int32_t x = b + glane; x < e; x += group) relax(cw[x], x);
+      } else {  // edges from L2: two per lane and round, both loads issued before either is used
+        for (int32_t x = b + glane; x < e; x += 2 * group) {
+          const int32_t x1 = x + group;
+          const uint2 c0 = cw[x];
+          const uint2 c1 = x1 < e ? cw[x1] : make_uint2(0u, 0u);
+          relax(c0, x);
+          if (x1 < e) relax(c1, x1);
+        }
       }
     }
     __syncthreads();
-    edges_cur = 0;
-    count = small_build(n, rp, bm, front, sc, &edges_cur, &updates);
+    count = small_build(n, ho, bm, front, sc, &updates);
   }
 
   // 4. Outputs.
