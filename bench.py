@@ -1077,11 +1077,14 @@ def main_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": wl.wtype, "data": "synthetic",
-            "config": {"workload": wl.name, "n": wl.n, "m": wl.m, "e_wcc": wl.e_wcc,
-                       "sources_per_step": len(step_sources)},
+            # the workload of the GPU arm's line, key for key; what one timed step of
+            # this arm solves is the sample below
+            "config": {"workload": wl.name, "n": wl.n, "m": wl.m, "e_wcc": wl.e_wcc, "s_wcc": wl.s_wcc,
+                       "sources_per_step": len(wl.sources) * args.gpus, "parallelism": f"replicas{args.gpus}",
+                       "l2": l2_rule(wl.n, wl.m, l2_bytes(0))[1]},
             "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": threads, "kind": "oracle",
-                             "sample": f"{len(step_sources)} sources per step, literal GOVM (Algorithm 2), "
-                                       f"one source per thread"},
+                             "sample": f"{len(step_sources)} of the workload's {len(wl.sources)} sources per step, "
+                                       f"literal GOVM (Algorithm 2), one source per thread"},
             "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
