@@ -534,6 +534,12 @@ def run_e2e(args, wl, device, world, tuning=None):
             "d2h_bytes_per_step": int(d2h), "steps": steps, "ms_per_step": el / steps * 1e3,
             "copies_alone_ms": {"d2h": d2h_ms, "h2d": h2d_ms, "d2h_gbs": d2h / d2h_ms / 1e6,
                                 "h2d_gbs": h2d / h2d_ms / 1e6},
+            # the same metric from the median step's host wall time (the first
+            # step's graph upload excluded): a step that met a slow host link
+            # moves the mean, not this
+            "median_step_value": S * world * wl.e_wcc / (float(np.median(
+                [st["enqueue_ms"] + st["ingest_next_ms"] + st["status_and_destroy_ms"] for st in phases["steps"]]))
+                / 1e3) / 1e9,
             "phases": phases}
 
 
