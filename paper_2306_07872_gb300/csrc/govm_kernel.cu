@@ -68,6 +68,7 @@ struct BlockShared {
   unsigned long long scan[kWarpsPerBlock];
   int32_t flag;
   int32_t any_mark;               // direct steps: some warp of the block made a strict improvement
+  uint32_t pool[kWarpsPerBlock];  // direct steps: marked vertices in each warp's words of the round
   unsigned long long trace_sum[2];  // direct steps of a traced solve: the block's frontier and edges this step
   unsigned long long bar_target;  // arrivals that end the next device-wide barrier (thread 0)
   WarpTile wt[kWarpsPerBlock];
@@ -576,11 +577,14 @@ __device__ __forceinline__ void relax_tile(const GovmParams &p, WarpTile &wt, in
 // g owns bitmap words g, g + W, g + 2W, ... (W = warps in the grid), 32 at a
 // time, one per lane: spreading each warp's words over the whole bitmap
 // keeps warps evenly loaded even where the frontier is spatially dense (a
-// grid's wavefront).  The warp clears its words, ranks their marked vertices
-// and expands them 32 at a time, one per lane: each lane reads its vertex's
+// grid's wavefront).  Each warp clears its words; the marked vertices of all
+// the block's words are ranked together (a block barrier), and every warp of
+// the block expands 32 of them at a time, one per lane, so a warp whose words
+// hold many marks does not expand them alone: each lane reads its vertex's
 // row bounds and, in place, its distance key; the 32 rows' out-edges are laid
 // end to end and relaxed in kTile-edge tiles with the same edge phase as
-// relax_tile.  Marks go to `bn`.  With p.skip_remarked, a vertex whose bit
+// relax_tile.  Must be reached by every thread of the block.  Marks go to
+// `bn`.  With p.skip_remarked, a vertex whose bit
 // in `bn` is already set (its distance dropped again earlier in this step)
 // is not expanded now: it is in the next frontier and is expanded there with
 // a key no larger.  Counters: `marked` (the vertices consumed), `front`
@@ -589,23 +593,26 @@ __device__ __forceinline__ void relax_tile(const GovmParams &p, WarpTile &wt, in
 // of the first round, which the caller loads before its stop test.  Returns
 // whether this warp made any strict improvement (a mark in bn).
 template <int WT>
-__device__ bool direct_step(const GovmParams &p, uint32_t *bm, uint32_t *bn, uint32_t first_bits, WarpTile &wt,
+__device__ bool direct_step(const GovmParams &p, uint32_t *bm, uint32_t *bn, uint32_t first_bits, BlockShared &sh,
                             unsigned long long &marked, unsigned long long &front, unsigned long long &edges,
                             unsigned long long &skipped) {
-  const int lane = threadIdx.x & 31;
-  const int64_t gwarp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  WarpTile &wt = sh.wt[warp];
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  // wt.ebase / wt.dkey hold the round's 32 entries in [0, 32); the words'
-  // bits and rank starts live above them
+  const int64_t bwarp0 = (int64_t)blockIdx.x * kWarpsPerBlock;  // the block's first warp in the grid
+  // wt.ebase / wt.dkey hold the round's 32 entries in [0, 32); the warp's
+  // words' bits and rank starts live above them, where the block's other
+  // warps read them too
   uint32_t *wbits = wt.ebase + 64;
   uint32_t *wstart = wt.dkey + 64;
   unsigned long long *st = p.state;
   unsigned strict_any = 0;
-  for (int64_t base = gwarp; base < p.words; base += 32 * nwarps) {  // warp-uniform
+  for (int64_t r = 0; bwarp0 + r < p.words; r += 32 * nwarps) {  // block-uniform
+    const int64_t base = bwarp0 + warp + r;             // this warp's first word of the round
     const int64_t w = base + (int64_t)lane * nwarps;  // this lane's word
     uint32_t bits = 0;
     if (w < p.words) {
-      bits = base == gwarp ? first_bits : __ldcg(bm + w);  // the first round's word was loaded by the caller
+      bits = r == 0 ? first_bits : __ldcg(bm + w);  // the first round's word was loaded by the caller
       if (bits) bm[w] = 0u;  // consumed: this bitmap receives the marks of the next step
     }
     const uint32_t pc = __popc(bits);
@@ -616,27 +623,44 @@ __device__ bool direct_step(const GovmParams &p, uint32_t *bm, uint32_t *bn, uin
       const uint32_t o = __shfl_up_sync(kFull, incl, d);
       if (lane >= d) incl += o;
     }
-    const uint32_t T = __shfl_sync(kFull, incl, 31);
-    if (T == 0) continue;  // warp-uniform
-    __syncwarp();  // the previous round of this warp has finished with wt
     wbits[lane] = bits;
     wstart[lane] = incl - pc;
-    __syncwarp();
-    for (uint32_t r0 = 0; r0 < T; r0 += 32) {  // warp-uniform
-      const uint32_t rank = r0 + lane;
+    if (lane == 31) sh.pool[warp] = incl;
+    __syncthreads();
+    // The block's marked vertices are ranked across its warps (warp s's
+    // words first, then warp s + 1's), and every warp expands 32 of them per
+    // round: a warp whose words hold many marks no longer expands them alone.
+    uint32_t cnt = lane < kWarpsPerBlock ? sh.pool[lane] : 0u;
+    uint32_t sincl = cnt;
+#pragma unroll
+    for (int d = 1; d < kWarpsPerBlock; d <<= 1) {
+      const uint32_t o = __shfl_up_sync(kFull, sincl, d);
+      if (lane >= d) sincl += o;
+    }
+    const uint32_t sstart = sincl - cnt;  // lanes below kWarpsPerBlock: warp `lane`'s first rank
+    const uint32_t T = __shfl_sync(kFull, sincl, kWarpsPerBlock - 1);
+    for (uint32_t r0 = 0; r0 < T; r0 += kBlockThreads) {  // block-uniform
+      const uint32_t rank = r0 + (uint32_t)warp * 32 + lane;
+      int32_t owner = 0;  // warp whose words hold this rank: the largest with a start at or below it
+#pragma unroll
+      for (int q = 1; q < kWarpsPerBlock; ++q)
+        if (__shfl_sync(kFull, sstart, q) <= rank) owner = q;
+      const uint32_t orank = rank - __shfl_sync(kFull, sstart, owner);
       int32_t v = -1;
       if (rank < T) {
-        int32_t a = 0, b = 32;  // lane whose word holds this rank: largest a with wstart[a] <= rank
+        const uint32_t *obits = sh.wt[owner].ebase + 64;
+        const uint32_t *ostart = sh.wt[owner].dkey + 64;
+        int32_t a = 0, b = 32;  // lane whose word holds this rank: largest a with ostart[a] <= orank
         while (b - a > 1) {
           const int32_t mid = (a + b) >> 1;
-          if (wstart[mid] <= rank) a = mid; else b = mid;
+          if (ostart[mid] <= orank) a = mid; else b = mid;
         }
-        uint32_t m = wbits[a];
-        for (uint32_t skip = rank - wstart[a]; skip > 0; --skip) m &= m - 1;
+        uint32_t m = obits[a];
+        for (uint32_t skip = orank - ostart[a]; skip > 0; --skip) m &= m - 1;
         if (m == 0) {  // cannot happen: every rank below T has a marked bit
           set_status(p.ctl, DAWN_ERR_BOUNDS);
         } else {
-          v = (int32_t)((base + (int64_t)a * nwarps) * 32 + __ffs(m) - 1);
+          v = (int32_t)((bwarp0 + owner + r + (int64_t)a * nwarps) * 32 + __ffs(m) - 1);
         }
       }
       uint32_t rs = 0, deg = 0;
@@ -689,6 +713,7 @@ __device__ bool direct_step(const GovmParams &p, uint32_t *bm, uint32_t *bn, uin
         strict_any |= __any_sync(kFull, strict != 0);
       }
     }
+    __syncthreads();  // every warp is done with the round's words before the next round rewrites them
   }
   return strict_any != 0;
 }
@@ -798,8 +823,8 @@ __global__ void __launch_bounds__(kBlockThreads, MINB) govm_kernel(GovmParams p)
         ctl->marks[(step + 1) % 3] = 0u;  // set in step + 1, read two steps from now
       }
       const unsigned long long f0 = front, e0 = edges;
-      const bool any = direct_step<WT>(p, bm_cur, p.bitmap + (size_t)((step + 1) & 1) * p.words, first_bits,
-                                       sh.wt[warp], step == 0 ? seeded : updates, front, edges, skipped);
+      const bool any = direct_step<WT>(p, bm_cur, p.bitmap + (size_t)((step + 1) & 1) * p.words, first_bits, sh,
+                                       step == 0 ? seeded : updates, front, edges, skipped);
       if (any && lane == 0) sh.any_mark = 1;
       if (p.trace) {  // traced solves keep the cumulative counters current per step
         unsigned long long df = front - f0, de = edges - e0;
