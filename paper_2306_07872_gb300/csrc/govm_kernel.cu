@@ -579,8 +579,9 @@ __device__ __forceinline__ void relax_tile(const GovmParams &p, WarpTile &wt, in
 // keeps warps evenly loaded even where the frontier is spatially dense (a
 // grid's wavefront).  Each warp clears its words; the marked vertices of all
 // the block's words are ranked together (a block barrier), and every warp of
-// the block expands 32 of them at a time, one per lane, so a warp whose words
-// hold many marks does not expand them alone: each lane reads its vertex's
+// the block expands up to 32 of them at a time (a round's ranks split evenly
+// over the warps), one per lane, so a warp whose words hold many marks does
+// not expand them alone: each lane reads its vertex's
 // row bounds and, in place, its distance key; the 32 rows' out-edges are laid
 // end to end and relaxed in kTile-edge tiles with the same edge phase as
 // relax_tile.  Must be reached by every thread of the block.  Marks go to
@@ -640,14 +641,17 @@ __device__ bool direct_step(const GovmParams &p, uint32_t *bm, uint32_t *bn, uin
     const uint32_t sstart = sincl - cnt;  // lanes below kWarpsPerBlock: warp `lane`'s first rank
     const uint32_t T = __shfl_sync(kFull, sincl, kWarpsPerBlock - 1);
     for (uint32_t r0 = 0; r0 < T; r0 += kBlockThreads) {  // block-uniform
-      const uint32_t rank = r0 + (uint32_t)warp * 32 + lane;
+      // the round's ranks split evenly over the warps, consecutive ranks per
+      // warp (a round of fewer than 256 ranks still keeps every warp busy)
+      const uint32_t per = (min(T - r0, (uint32_t)kBlockThreads) + kWarpsPerBlock - 1) / kWarpsPerBlock;
+      const uint32_t rank = r0 + (uint32_t)warp * per + lane;
       int32_t owner = 0;  // warp whose words hold this rank: the largest with a start at or below it
 #pragma unroll
       for (int q = 1; q < kWarpsPerBlock; ++q)
         if (__shfl_sync(kFull, sstart, q) <= rank) owner = q;
       const uint32_t orank = rank - __shfl_sync(kFull, sstart, owner);
       int32_t v = -1;
-      if (rank < T) {
+      if (lane < (int)per && rank < T) {
         const uint32_t *obits = sh.wt[owner].ebase + 64;
         const uint32_t *ostart = sh.wt[owner].dkey + 64;
         int32_t a = 0, b = 32;  // lane whose word holds this rank: largest a with ostart[a] <= orank
