@@ -496,10 +496,10 @@ def run_e2e(args, wl, device, world, tuning=None):
                                 "device_gap_before_ms": rows[i - 1][3][1].elapsed_time(ev[0]) if i else None}
                                for i, (a, b, c, ev) in enumerate(rows)]
 
-    # warm-up: two steps, so that two graphs have been alive at once and the
-    # library's memory pool holds what the loop needs (a pool that grows maps
-    # new memory while solves run, which can stall them)
-    run(2)
+    # warm-up: the line's W steps (at least two, so that two graphs have been
+    # alive at once and the library's memory pool holds what the loop needs: a
+    # pool that grows maps new memory while solves run, which can stall them)
+    run(max(2, args.warmup))
     torch.cuda.synchronize()
     steps = max(1, min(args.steps, 10))  # the line's K steps, at most 10
     barrier(world)
