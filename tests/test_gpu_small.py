@@ -159,3 +159,49 @@ def test_small_kernel_compact_apsp_against_floyd_warshall(dawn):
     g = dawn.Graph(wl.row_ptr, wl.col, wl.weights)
     D, _ = g.msssp(np.arange(wl.n, dtype=np.int32), parent=False)
     assert np.array_equal(D.cpu().numpy(), oracle.floyd_warshall(wl.row_ptr, wl.col, wl.weights))
+
+
+def hub_graph(seed, hubs=300, hub_deg=300, n=8192):
+    """A source with an edge to each of `hubs` hubs, each hub with `hub_deg`
+    out-edges to random vertices, and a sparse random background: hundreds of
+    vertices in one frontier with far more out-edges than a thread group
+    takes."""
+    rng = np.random.default_rng(seed)
+    hub_ids = rng.choice(np.arange(1, n), size=hubs, replace=False)
+    src, dst = [np.zeros(hubs, np.int64)], [hub_ids.astype(np.int64)]
+    for h in hub_ids:
+        src.append(np.full(hub_deg, h, np.int64))
+        dst.append(rng.integers(0, n, hub_deg))
+    bg = 2 * n
+    src.append(rng.integers(0, n, bg))
+    dst.append(rng.integers(0, n, bg))
+    src, dst = np.concatenate(src), np.concatenate(dst)
+    order = np.lexsort((dst, src))
+    src, dst = src[order], dst[order]
+    rp = np.zeros(n + 1, np.int32)
+    np.add.at(rp, src + 1, 1)
+    rp = np.cumsum(rp).astype(np.int32)
+    w = rng.integers(1, 50, len(dst)).astype(np.uint32)
+    return rp, dst.astype(np.int32), w
+
+
+@pytest.mark.parametrize("parents", [True, False])
+def test_small_kernel_many_hubs_in_one_frontier(dawn, parents):
+    # 300 hubs enter the frontier together, each with about 19 times the
+    # average out-degree; distances (compact form without parents, packed
+    # form with them) and parents must equal the oracle's
+    rp, cl, w = hub_graph(46)
+    n = len(rp) - 1
+    g = dawn.Graph(rp, cl, w)
+    g.set_option(dawn.DAWN_OPT_SMALL_PATH, dawn.DAWN_SMALL_WHEN_STATE_FITS)
+    src = torch.tensor([0, 7, 1234], dtype=torch.int32, device="cuda")
+    D = torch.empty((3, n), dtype=torch.uint32, device="cuda")
+    P = torch.empty((3, n), dtype=torch.int32, device="cuda") if parents else None
+    dawn.dawn_msssp(g.handle, src, D, P)
+    g.check()
+    for i, s in enumerate((0, 7, 1234)):
+        d_ref, p_ref, _ = oracle.sssp(rp, cl, w, s)
+        assert np.array_equal(D[i].cpu().numpy(), d_ref), i
+        if parents:
+            assert np.array_equal(P[i].cpu().numpy(), p_ref), i
+    g.close()
