@@ -1071,7 +1071,7 @@ def main_reference(args):
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
     threads = max(1, min(cores, 16))
     t, _ = oracle.timed_govm(wl.row_ptr, wl.col, wl.weights, [int(wl.sources[0])], threads=1)
-    per_step = max(1, min(len(wl.sources), threads * max(1, int(8.0 / max(t, 1e-3)))))
+    per_step = max(1, min(len(wl.sources), threads * max(1, int(4.0 / max(t, 1e-3)))))  # about 4 s per thread
     step_sources = [int(s) for s in wl.sources[:per_step]]
     for _ in range(args.warmup):
         oracle.timed_govm(wl.row_ptr, wl.col, wl.weights, step_sources[:threads], threads=threads)
