@@ -605,6 +605,8 @@ def leg_msssp(args, device=0):
     import graphgen as gg
     import paper_2306_07872_gb300 as dawn
     wl = gg.rmat_u32(18, 16, nsrc=1024, seed=0)
+    if args.sources:  # a smaller batch (profiling runs)
+        wl.sources = wl.sources[:args.sources]
     g = dawn.Graph(wl.row_ptr, wl.col, wl.weights)
     src = torch.from_numpy(wl.sources).cuda()
     k = len(wl.sources)
