@@ -103,9 +103,10 @@ typedef struct {
  * Validation runs on the device and is synchronous (the call waits for it).
  * Device memory: every buffer of a handle (the graph, the solver workspace,
  * the backward scratch, staging and trace buffers) comes from a stream-ordered
- * memory pool per device that the library owns; no call allocates with
- * cudaMalloc or frees with cudaFree, so no allocation or free synchronises
- * the device.
+ * memory pool per device that the library owns; creation, solves, the
+ * backward pass and destruction never call cudaMalloc or cudaFree, so none of
+ * their allocations or frees synchronises the device (dawn_autotune, a setup
+ * call, allocates its own timing scratch with cudaMalloc).
  * Memory a handle frees stays in the pool and serves later allocations
  * without mapping new memory; dawn_trim_memory returns it to the devices.
  * Allocations are refused (DAWN_ERR_CUDA) on a stream that is being
@@ -334,7 +335,8 @@ int dawn_set_option(dawn_graph g, int option, int64_t value);
  * two builds of the persistent kernel (4 or 5 CTAs per SM) times the grid
  * sizes {all co-resident CTAs, 3/4, 1/2, 1/4 of them, one per SM, the
  * automatic size}, times, in DAWN_TUNE_MSSSP mode, the batch sizes {largest,
- * 1/2, 1/4 of it}; in the single-instance modes, the step form that
+ * 1/2, 1/4 of it}, plus batches of 16, 8 and 4 instances (below k) with each
+ * build at the automatic grid size; in the single-instance modes, the step form that
  * DAWN_FRONTIER_AUTO does not pick (queue or bitmap steps, DAWN_OPT_FRONTIER)
  * with each build at the automatic grid size; and the small-graph kernel
  * when the graph's solver state fits in shared memory (DAWN_OPT_SMALL_PATH).  Results do not depend on
