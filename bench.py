@@ -824,6 +824,42 @@ def run_diff(args):
     return {"diff_rmat16_f32": leg_diff(args)}
 
 
+def leg_c2_batched(args, wl, res, device=0):
+    """The headline workload's sources solved in batched dawn_msssp launches,
+    in the batch size the autotuner picks, against the line's own single
+    solves (`res`): the metric's batched-vs-plain comparison on the C2 graph.
+    Distances are compared bit for bit with the line's single solves, which
+    the line's cpu_baseline compares with the oracle."""
+    import torch
+    import paper_2306_07872_gb300 as dawn
+    g = dawn.Graph(wl.row_ptr, wl.col, wl.weights, device=device)
+    k = len(wl.sources)
+    src = torch.from_numpy(wl.sources).to(device)
+    dist = torch.empty((k, wl.n), dtype=torch.uint32, device=device)
+    par = torch.empty((k, wl.n), dtype=torch.int32, device=device)
+    tune = None if args.no_tune else g.autotune(wl.sources, mode="msssp", reps=2)
+    flush_needed, l2note = l2_rule(wl.n, wl.m, l2_bytes(device))
+    flush = L2Flush(device) if flush_needed else None
+    with Clocks(device) as clk:
+        tb = timed_calls(lambda: dawn.dawn_msssp(g.handle, src, dist, par), max(1, min(args.steps, 5)), flush=flush)
+        g.check()
+    st = g.stats()
+    t_batch = float(tb.mean())
+    t_single = res["launch_ms_mean"] / 1e3 * k  # the line's single solves of the same sources
+    out = {"batched_s": t_batch, "single_solves_s": t_single, "speedup": t_single / t_batch,
+           "gteps_batched": k * wl.e_wcc / t_batch / 1e9, "tuning": tune, "clocks": clk.summary(), "l2": l2note,
+           "config": {"workload": wl.name, "n": wl.n, "m": wl.m, "e_wcc": wl.e_wcc, "sources": k,
+                      "timed_calls": len(tb)},
+           "roofline": roofline_entry(bytes_alg(st), t_batch, f"govm_kernel ({k} instances)",
+                                      ALG_RULE + ", summed over the instances")}
+    if res.get("dist_host") is not None:
+        out["bit_exact_vs_single_solves"] = bool(np.array_equal(dist.cpu().numpy(), res["dist_host"]))
+    del dist, par
+    g.close()
+    torch.cuda.empty_cache()
+    return out
+
+
 def leg_grid(args, device=0):
     """C3: the 2048^2 fp32 grid with 1 % shortcuts, 16 sources each solved as
     its own SSSP (many GOVM steps with small frontiers)."""
@@ -1153,6 +1189,9 @@ def main_ours(args):
             # the rest of the metric: high-diameter, batched and
             # differentiable forms beside the plain solver, each with its own
             # clocks, roofline and oracle leg
+            t = time.time()
+            line["msssp_rmat22_64"] = leg_c2_batched(args, wl, res, device)
+            log(f"[bench] leg msssp_rmat22_64 done in {time.time() - t:.1f} s")
             for key, fn in (("grid_2048_f32", leg_grid), ("msssp_rmat18_1024", leg_msssp),
                             ("roots_er64", leg_roots), ("diff_rmat16_f32", leg_diff)):
                 t = time.time()
