@@ -249,9 +249,9 @@ int dawn_get_stats(dawn_graph g, dawn_stats *out);
  *                          registers, 32 warps); 0 = default, others invalid
  *   DAWN_OPT_BATCH         instances per persistent launch in dawn_msssp
  *                          (0 = as many as the workspace budget allows, or,
- *                          when one instance's 8-byte-per-vertex state takes
- *                          more than an eighth of L2, as many as fit L2
- *                          together and at least 4)
+ *                          when fewer than 32 instances' 8-byte-per-vertex
+ *                          states fit L2 together, as many as fit and at
+ *                          least 4)
  *   DAWN_OPT_TEST_STALL    1: block 0 waits on a flag nothing sets, so the
  *                          bounded waits run out (tests DAWN_ERR_TIMEOUT)
  *   DAWN_OPT_SMALL_PATH    DAWN_SMALL_AUTO (default): a graph whose solver

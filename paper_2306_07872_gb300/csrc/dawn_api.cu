@@ -709,12 +709,13 @@ int dawn_msssp(dawn_graph g, const int32_t *sources, int32_t k, void *dist, int3
   int32_t chunk = g->batch > 0 ? std::min({k, g->batch, max_chunk(g)})
                                : std::min(k, g->ws_k > 0 ? std::max(g->ws_k, std::min(k, max_chunk(g)))
                                                          : max_chunk(g));
-  // Automatic batch on a graph whose packed state takes more than an eighth
-  // of L2: as many instances per launch as fit L2 together (at least 4), so
-  // that their state gathers stay L2 hits (R-MAT s22: 4 or 8 per launch run
-  // 1.4x faster than 64).
+  // Automatic batch on a graph where fewer than 32 instances' packed states
+  // fit L2 together: as many instances per launch as fit (at least 4), so
+  // that their state gathers stay L2 hits (R-MAT s20 16 and s22 4 per launch:
+  // 1.32x and 1.39x faster than the largest batch).  With smaller states the
+  // largest batch is fastest (R-MAT s18: 512 per launch, 64 fit L2).
   const int64_t state = 8 * (int64_t)g->n;
-  if (g->batch <= 0 && g->l2_bytes > 0 && state * 8 > g->l2_bytes)
+  if (g->batch <= 0 && g->l2_bytes > 0 && state * 32 > g->l2_bytes)
     chunk = (int32_t)std::max<int64_t>(1, std::min<int64_t>(chunk, std::max<int64_t>(4, g->l2_bytes / state)));
   g->last_k = k;
   for (int32_t b = 0; b < k; b += chunk) {
