@@ -100,7 +100,7 @@ def _bench_commands(text):
 
 
 def test_profile_commands_run_committed_files_with_current_flags():
-    known = {"grid", "tiny", "batched", "diff", "mu", "apsp", "gsvm"}
+    known = {"grid", "tiny", "batched", "batched22", "diff", "mu", "apsp", "gsvm"}
     pdir = os.path.join(ROOT, "profiles")
     files = sorted(f for f in os.listdir(pdir) if f.endswith(".md"))
     assert files
