@@ -142,3 +142,25 @@ def test_msssp_captured_in_cuda_graph(dawn, Graph):
     torch.cuda.synchronize()
     assert dawn.dawn_status(g.handle) == 0
     exact_rows(wl, wl.sources, dist.cpu().numpy(), par.cpu().numpy())
+
+
+def test_msssp_automatic_batch_on_a_graph_larger_than_l2(dawn):
+    # on R-MAT s20 fewer than 32 instances' packed states (8 MB each) fit L2
+    # together, so the automatic batch splits 24 sources into launches of as
+    # many as fit; every row must equal the single-source solve, and sampled
+    # rows the oracle
+    wl = gg.rmat_u32(20, 16, nsrc=24, seed=12)
+    g = dawn.Graph(wl.row_ptr, wl.col, wl.weights)
+    g.set_option(dawn.DAWN_OPT_SMALL_PATH, dawn.DAWN_SMALL_NEVER)
+    D, P = g.msssp(wl.sources)
+    D, P = D.cpu().numpy(), P.cpu().numpy()
+    assert g.stats()["instances"] == len(wl.sources)
+    for i, s in enumerate(wl.sources):
+        d1, p1, _ = g.sssp(int(s), parent=True)
+        assert np.array_equal(D[i], d1.cpu().numpy()), i
+        assert np.array_equal(P[i], p1.cpu().numpy()), i
+    for i in (0, 23):
+        d_ref, p_ref, _ = oracle.sssp(wl.row_ptr, wl.col, wl.weights, int(wl.sources[i]))
+        assert np.array_equal(D[i], d_ref), i
+        assert np.array_equal(P[i], p_ref), i
+    g.close()
