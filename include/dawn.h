@@ -430,10 +430,10 @@ int dawn_sssp_noalloc(dawn_graph g, int32_t source, void *dist, int32_t *parent,
 /* Human-readable name of a status code (static string; plumbing). */
 const char *dawn_status_string(int code);
 
-/* Free the graph and its device memory.  Waits for the handle's last stream,
- * then returns its buffers to the library's pool (see dawn_create_graph),
- * where they stay for later handles until dawn_trim_memory.
- * NULL is allowed (plumbing). */
+/* Free the graph and its device memory.  Waits for the handle's last stream
+ * (the stream of its last call, which must still exist), then returns its
+ * buffers to the library's pool (see dawn_create_graph), where they stay for
+ * later handles until dawn_trim_memory.  NULL is allowed (plumbing). */
 void dawn_destroy(dawn_graph g);
 
 /* Return to the devices the memory of the library's pools that no handle
